@@ -1,0 +1,327 @@
+#!/usr/bin/env python
+"""Throughput of the forward + inverse SHT on GB300 (one JSON line on stdout, rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--L 1024] [--batch 64]
+
+A step is one inverse SHT (coefficients -> samples) followed by one forward SHT (samples ->
+coefficients) of a batch of synthetic signals: every stage of the path (ring DFTs, the order
+chain with its solves and alias subtractions, the synthesis contraction, the fold and inverse
+ring DFTs) runs once per step.  Default workload: 64 complex signals at L = 1024, f_l^m re/im iid
+N(0,1) * (l+1)^-1, plain float64.  Inputs (1 GiB per buffer) are larger than L2.
+
+Under torchrun (N > 1) every rank transforms its own batch (weak scaling, no collective on the
+data path); the time is the max over ranks.
+
+--impl reference times the plain float64 CPU oracle on this host (rank 0 only): each step is a
+bounded sample of the same workload - one signal, the last 1/16 of the orders of Procedure 2's
+loop and the first 1/16 of the iterations of Procedure 1's loop - scaled to signals/s.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+inv SHT signals/s at L=1024 vs FP64 oracle error; % tensor-pipe peak"
+SAMPLE_FRACTION = 16  # the reference arm runs 1/16 of the order loop of each procedure
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f)
+    return {}
+
+
+# float64 pipe of a GB300: 1.25 TFLOP/s at the 2070 MHz boost clock (NVIDIA's figure, which the
+# FFMA64 microbenchmark recorded in profiles/fp64_peak.md reproduces); scaled by the measured clock.
+FP64_TFLOPS_NOMINAL = 1.25
+FP64_NOMINAL_MHZ = 2070.0
+
+
+def _traffic_record(kernel, L, batch):
+    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel/workload."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = dict(p.split("=", 1) for p in line.split() if "=" in p)
+        if parts.get("kernel") == kernel and parts.get("L") == str(L) and parts.get("batch") == str(batch):
+            return float(parts["dram_bytes_per_launch"])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def _oracle_sample(L, seed, frac):
+    """One bounded oracle sample: returns seconds for 1/frac of each procedure's order loop."""
+    from oracle import sht as osht
+    from oracle import sampling
+    from paper_1403_4661_gb300 import synth
+    from tests.helpers import oracle_order
+
+    theta = sampling.equiangular_set(L)[oracle_order(L)]
+    c = synth.decaying_coeffs(L, 1, seed)
+    m_lo = L - L // frac
+    t0 = time.perf_counter()
+    s = osht.inverse(c, L, theta, m_lo=m_lo)
+    osht.forward(s, L, theta, m_lo=m_lo)
+    return time.perf_counter() - t0
+
+
+def _cpu_baseline_subprocess(L, frac, steps):
+    """Time the oracle in a fresh single-threaded process (spawned, before it touches the GPU)."""
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps([bench._oracle_sample(%d, 100 + i, %d) for i in range(%d)]))"
+            % (ROOT, L, frac, steps))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    if r.returncode != 0:
+        raise RuntimeError("oracle timing failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args):
+    dist, rank, ws, _ = _dist() if int(os.environ.get("WORLD_SIZE", "1")) > 1 else (None, 0, 1, 0)
+    if rank != 0:
+        return
+    times = _cpu_baseline_subprocess(args.L, SAMPLE_FRACTION, args.warmup + args.steps)[args.warmup:]
+    per_signal = statistics.mean(times) * SAMPLE_FRACTION
+    value = 1.0 / per_signal
+    sample = (f"1 signal at L={args.L}; last 1/{SAMPLE_FRACTION} of Procedure 2's order loop and first "
+              f"1/{SAMPLE_FRACTION} of Procedure 1's, x{SAMPLE_FRACTION}; the sampled orders are the "
+              "cheap ones (measured at L=512: full run 1.5x the scaled 1/8 sample)")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "signals/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * per_signal * args.batch, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args),
+        "cpu_baseline": {"value": value, "unit": "signals/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "signals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(args):
+    return {"workload": f"{args.batch} complex signals at L={args.L}, f_lm re/im iid N(0,1)/(l+1); "
+                        "inverse SHT then forward SHT, plain float64",
+            "L": args.L, "batch_per_gpu": args.batch, "ordering": "greedy (Sec. III-E)",
+            "l2": "inputs larger than L2 (16 L^2 B bytes per buffer), no flush"}
+
+
+def run_ours(args):
+    import torch
+
+    from paper_1403_4661_gb300 import build, synth
+    from paper_1403_4661_gb300.sht import Plan
+
+    dist, rank, ws, local = _dist()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    L, B = args.L, args.batch
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle in a spawned single-threaded process, before the GPU work starts
+        t = _cpu_baseline_subprocess(L, SAMPLE_FRACTION, 1)
+        cpu = {"value": 1.0 / (t[0] * SAMPLE_FRACTION), "unit": "signals/s", "cores": 1, "kind": "oracle",
+               "sample": f"1 signal at L={L}; last 1/{SAMPLE_FRACTION} of Procedure 2's order loop and "
+                         f"first 1/{SAMPLE_FRACTION} of Procedure 1's, x{SAMPLE_FRACTION} (the sampled "
+                         "orders are the cheap ones: this overstates the oracle's speed ~1.5x)"}
+
+    t0 = time.time()
+    plan = Plan(L)  # greedy ring ordering on the GPU, tables, per-order inverses
+    plan_s = time.time() - t0
+    plan.reserve(B)
+    c_host = torch.from_numpy(synth.decaying_coeffs(L, B, 1000 + rank)).pin_memory()
+    c = c_host.to(dev)
+    s = torch.empty_like(c)
+    c2 = torch.empty_like(c)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    err = (c2 - c).abs().max().item()
+
+    # ---- device-resident timed region --------------------------------------------------------
+    plan.set_timing(True)
+    plan.stage_times()
+    launches0 = plan.info()["kernel_launches"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = plan.info()["kernel_launches"] - launches0
+    stages = plan.stage_times()
+    plan.set_timing(False)
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    # ---- end to end: host buffers, copies inside the timed region ----------------------------
+    out_host = torch.empty_like(c_host).pin_memory()
+
+    def step_e2e():
+        c.copy_(c_host, non_blocking=True)
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+        out_host.copy_(c2, non_blocking=True)
+
+    step_e2e()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step_e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = t.item()
+    err_e2e = float(np.abs(out_host.numpy() - c_host.numpy()).max())
+
+    if rank != 0:
+        return
+    # ---- roofline of the dominant kernel: the synthesis contraction (one launch per inverse) --
+    syn_ms, syn_n = stages["synthesis"]
+    flops = 4.0 * B * L * L * (L + 1)     # sum_m 2 * L * (L - m) * 4B real multiply-adds
+    achieved = flops / (syn_ms / syn_n * 1e-3) / 1e12
+    sm_mhz = (clk or {}).get("sm_mhz") or FP64_NOMINAL_MHZ
+    peak = FP64_TFLOPS_NOMINAL
+    roof = {"bound": "alu", "kernel": "k_gemm<64,64,false,EPI_STORE,MODE_SYNTH> (float64 synthesis, Eq. (11))",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_source": "GB300 float64 pipe, 1.25 TFLOP/s at 2070 MHz (DESIGN.md); at the measured "
+                           f"median {sm_mhz:.0f} MHz the clock-scaled peak is {peak * sm_mhz / FP64_NOMINAL_MHZ:.3f}",
+            "traffic": _traffic_record("synthesis_f64", L, B),
+            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+            "stage_launch_spans_per_step": {k: v[1] / args.steps for k, v in stages.items()}}
+    value = ws * B / (ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": dict(_config(args), parallelism=f"dp{ws}" if ws > 1 else "single GPU"),
+        "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": ws * B / (ms_e2e * 1e-3), "unit": "signals/s",
+                "h2d_bytes_per_step": 16 * L * L * B, "d2h_bytes_per_step": 16 * L * L * B},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "plan_seconds": plan_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

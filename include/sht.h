@@ -1,0 +1,185 @@
+/*
+ * sht.h - C ABI of libsht: forward and inverse spherical harmonic transforms on the
+ * optimal-dimensionality sampling of Khalid, Kennedy and McEwen (L^2 samples on L rings),
+ * computed on one NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Sampling (Sec. III-A, Eqs. (7)-(9)): L rings at co-latitudes theta_0..theta_{L-1}; ring k
+ *    carries 2k+1 samples at phi_{k,n} = 2 pi n/(2k+1), n = 0..2k.  A signal is L^2 complex
+ *    values, ring-major: sample (k, n) at index k^2 + n.
+ *  Coefficients (Eq. (6)): f_l^m for 0 <= l < L, |m| <= l, at index l^2 + l + m.
+ *  Basis (Appendix A, Eq. (29)): orthonormal Y_l^m with the Condon-Shortley phase;
+ *    P~_l^m(theta) = Y_l^m(theta, 0).
+ *  Element type: complex128, interleaved (re, im) doubles - the layout of torch.complex128 and
+ *    C99 double _Complex.  A batch of B signals is B consecutive blocks of L^2 elements.
+ *  Device pointers must be 16-byte aligned; input and output must not overlap.
+ *  Ownership: the caller owns every buffer it passes.  The plan owns its tables (the P~ table and
+ *    the per-order inverses, allocated at plan creation) and its workspaces (allocated on the
+ *    first call that needs them, or by sht_plan_reserve, and kept until sht_plan_destroy).
+ *  Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Calls
+ *    are asynchronous and stream-ordered; after a call returns SHT_OK the result is valid once
+ *    the stream has reached that point.  A plan's workspaces are shared by all calls on it, so
+ *    calls on one plan must not overlap in time (use one stream per plan, or one plan per stream).
+ *    A call that finds its workspaces large enough allocates nothing and does not synchronise.
+ *  Errors: no entry point aborts.  Argument errors return SHT_ERR_INVALID_ARG (or
+ *    SHT_ERR_UNSUPPORTED) before any work is queued; a failed CUDA call returns SHT_ERR_CUDA
+ *    (the CUDA error string is kept for sht_last_error_message); allocation failure returns
+ *    SHT_ERR_OOM.  The current CUDA device must be the one the plan was created on.
+ */
+#ifndef SHT_H
+#define SHT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sht_plan_s *sht_plan_t;
+
+typedef enum {
+    SHT_OK = 0,
+    SHT_ERR_INVALID_ARG = 1,
+    SHT_ERR_UNSUPPORTED = 2,
+    SHT_ERR_OOM = 3,
+    SHT_ERR_CUDA = 4,
+    SHT_ERR_NOT_CONVERGED = 5,
+    SHT_ERR_TIMEOUT = 6
+} sht_status;
+
+/* Arithmetic of the transforms.  SHT_F64: every step in float64 (FP64 pipe). */
+typedef enum {
+    SHT_F64 = 0
+} sht_dtype;
+
+/* Plan flags: ring ordering (Sec. III-E). */
+#define SHT_ORDER_GREEDY 0u   /* condition-number minimisation: theta_{L-1} nearest the equator,
+                                 then for m = L-2..0 the unused ring minimising kappa_2(P_m)   */
+#define SHT_ORDER_SIMPLE 1u   /* Eq. (20): pi, then alternately north / south to the equator   */
+#define SHT_ORDER_MASK   1u
+
+#define SHT_MAX_L 2048   /* longest ring 4095: its chirp-z length 8192 fits one SM */
+
+/*
+ * sht_plan - build a plan for band-limit L (1 <= L <= SHT_MAX_L); batch is at most 65535.
+ *   Ring co-latitudes come from the equiangular set Theta_t = pi (2t+1)/(2L-1) (Eq. (19)),
+ *   ordered by the rule in `flags` (Sec. III-E).  The greedy ordering scores every candidate ring
+ *   by the exact 2-norm condition number of P_m (Eq. (12)) through the eigen-decomposition of the
+ *   fixed rows' Gram matrix and a rank-one secular equation; it costs O(L^4) and runs on the GPU.
+ *   Then builds, on the current device: the P~_l^m(theta_k) table for all m >= 0, k, l >= m
+ *   (L^3/2 doubles) and the explicit inverses of P_m for every m (L^3/3 doubles).
+ *   Blocking (synchronises the device).  *out receives the plan, or NULL on error.
+ */
+sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out);
+
+/*
+ * sht_plan_with_thetas - as sht_plan, with the L ring co-latitudes given by the caller (host
+ *   array of L doubles, theta_host[k] = theta_k in radians, any values in [0, pi] for which every
+ *   P_m is invertible; Remark 1).  The ordering bits of `flags` are ignored.
+ */
+sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host, uint32_t flags,
+                                sht_plan_t *out);
+
+/* sht_plan_thetas - copy the plan's L ring co-latitudes to theta_host_out (host, L doubles). */
+sht_status sht_plan_thetas(sht_plan_t plan, double *theta_host_out);
+
+/* sht_plan_bandlimit - the plan's L. */
+int sht_plan_bandlimit(sht_plan_t plan);
+
+/*
+ * sht_plan_reserve - allocate the workspaces for batches of up to `batch` signals now, so that
+ *   later calls with batch <= `batch` allocate nothing (required before capturing calls in a CUDA
+ *   graph).  Blocking.
+ */
+sht_status sht_plan_reserve(sht_plan_t plan, int64_t batch);
+
+/* sht_plan_destroy - free the plan and everything it owns (synchronises the device). */
+sht_status sht_plan_destroy(sht_plan_t plan);
+
+/*
+ * sht_forward - coefficients from samples (the forward SHT, Procedure 1 of Sec. III-C).
+ *   d_samples: device, batch * L^2 complex128, ring-major.   d_coeffs: device, batch * L^2.
+ *   Computed in bin space: every ring's DFT is taken once, then for m = L-1..0 the order-m system
+ *   g_m = P_m f_m (Eq. (14)) is solved with the plan's explicit inverse and the solved orders'
+ *   aliased contribution (Eq. (16)) is subtracted from the bins of the rings k < m (Eq. (15)).
+ *   batch >= 0 (0 is a no-op).
+ */
+sht_status sht_forward(sht_plan_t plan, const void *d_samples, void *d_coeffs, int64_t batch,
+                       void *stream);
+
+/*
+ * sht_inverse - samples from coefficients (the inverse SHT, Procedure 2 of Sec. III-D, Eq. (18)).
+ *   d_coeffs: device, batch * L^2 complex128.   d_samples: device, batch * L^2, ring-major.
+ *   G_m(theta_k) (Eq. (11)) for every order and ring, then per ring the fold of the 2L-1 orders
+ *   into the ring's 2k+1 frequency bins and an inverse DFT of length 2k+1.
+ */
+sht_status sht_inverse(sht_plan_t plan, const void *d_coeffs, void *d_samples, int64_t batch,
+                       void *stream);
+
+/*
+ * sht_inverse_adjoint - the adjoint A^H of the inverse map A (A[(k,n),(l,m)] = Y_l^m(theta_k,
+ *   phi_kn)): coefficients-shaped output from samples-shaped input,
+ *   out_l^m = sum_{k,n} P~_l^m(theta_k) e^{-i m phi_kn} y_kn.  Same layouts as sht_forward.
+ *   With PyTorch's convention this is the backward of sht_inverse.
+ */
+sht_status sht_inverse_adjoint(sht_plan_t plan, const void *d_samples, void *d_coeffs,
+                               int64_t batch, void *stream);
+
+/*
+ * sht_forward_adjoint - the adjoint (A^{-1})^H of the forward map: samples-shaped output from
+ *   coefficients-shaped input.  Runs the forward's order chain in reverse (m = 0..L-1) with the
+ *   transposed per-order inverses and alias gathers, then the adjoint ring DFTs.  Same layouts as
+ *   sht_inverse.  With PyTorch's convention this is the backward of sht_forward.
+ */
+sht_status sht_forward_adjoint(sht_plan_t plan, const void *d_coeffs, void *d_samples,
+                               int64_t batch, void *stream);
+
+/* Plan information. */
+typedef struct {
+    int L;
+    int dtype;
+    uint64_t table_bytes;      /* device bytes held by the plan's tables */
+    uint64_t workspace_bytes;  /* device bytes held by the plan's workspaces */
+    int64_t workspace_batch;   /* batch the workspaces are sized for */
+    double plan_seconds;       /* wall time of plan creation */
+    double order_seconds;      /* part of it spent ordering the rings */
+    int64_t kernel_launches;   /* kernels this plan's transform calls have launched so far */
+} sht_info;
+
+/* Stages of the transforms, for sht_plan_stage_times. */
+#define SHT_STAGE_RING_DFT   0  /* forward ring DFTs into bins (forward; adjoint of inverse)   */
+#define SHT_STAGE_SOLVE      1  /* per-order solves P_m^{-1} g_m (forward chain, all m)         */
+#define SHT_STAGE_ALIAS      2  /* alias subtractions from lower rings (forward chain, all m)   */
+#define SHT_STAGE_LAYOUT     3  /* coefficient <-> order-major conversions                      */
+#define SHT_STAGE_SYNTHESIS  4  /* G_m(theta_k) for all m, k (inverse; adjoint: analysis)       */
+#define SHT_STAGE_RING_IDFT  5  /* fold + inverse ring DFTs (inverse; adjoint of forward)       */
+#define SHT_NUM_STAGES       6
+
+/*
+ * sht_plan_set_timing - when enable != 0, later transform calls on this plan record a CUDA event
+ *   pair on the call's stream around each stage (no synchronisation, no allocation after the
+ *   first few calls).  Off by default.
+ */
+sht_status sht_plan_set_timing(sht_plan_t plan, int enable);
+
+/*
+ * sht_plan_stage_times - wait for the recorded events, write the summed milliseconds of each
+ *   stage to ms[SHT_NUM_STAGES] and the number of timed spans to spans[SHT_NUM_STAGES] (either
+ *   may be NULL), then clear the record.  Blocking on the recorded events only.
+ */
+sht_status sht_plan_stage_times(sht_plan_t plan, double *ms, int64_t *spans);
+
+sht_status sht_get_info(sht_plan_t plan, sht_info *out);
+
+/* Human-readable name of a status code (static string). */
+const char *sht_status_string(sht_status status);
+
+/* Detail of the last error raised on this thread (static per-thread buffer; "" if none). */
+const char *sht_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHT_H */

@@ -1,0 +1,372 @@
+// K1 / K5 / K7: ring DFTs of odd length N_k = 2k+1 and the order <-> bin fold, float64.
+//
+// Forward (Procedure 1, step 3; Eq. (11)): bin q in [-k, k] of ring k is
+//     H_k[q] = (1/N_k) sum_n s_k[n] e^{-2 pi i q n / N_k} = sum_{m = q mod N_k, |m| < L} G_m(theta_k),
+// so every ring is transformed once and the orders are separated later in bin space.
+// Inverse (Procedure 2; Eq. (18)): s_k[n] = sum_m G_m(theta_k) e^{i m phi_n}; orders congruent mod
+// N_k meet at the same sample values, so they are first folded into the N_k bins and one inverse
+// DFT of length N_k per ring finishes the sum.
+//
+// Ring lengths are odd and often prime.  Rings with N <= kDirectMaxN are transformed directly
+// (O(N^2), twiddles from a per-ring table of N roots).  Longer rings use Bluestein's chirp-z
+// identity  j n = (j^2 + n^2 - (j - n)^2) / 2: with c_n = e^{-i pi n^2 / N},
+//     X_j = c_j sum_n (x_n c_n) conj(c_{j-n}),
+// a linear convolution computed as a cyclic one of power-of-two length M >= 2N - 1 with a radix-2
+// FFT held in shared memory (one thread block per ring and signal).  c_n is evaluated from the
+// exactly reduced integer n^2 mod 2N, so no twiddle carries an argument-reduction error.
+// Rings are launched in classes k in [2^j, 2^(j+1)), which share M = 2^(j+3).
+#include "sht_internal.cuh"
+
+namespace sht {
+namespace {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -a.y); }
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
+// In-place radix-2 decimation-in-time FFT of a[0..M) in shared memory; natural-order input and
+// output.  tw[t] = e^{-2 pi i t / Mmax}; inverse = conjugate twiddles, unnormalised.
+__device__ void block_fft(double2 *a, int M, int logM, const double2 *__restrict__ tw, int Mmax,
+                          bool inverse) {
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+        int j = (int)(__brev((unsigned)i) >> (32 - logM));
+        if (i < j) { double2 t = a[i]; a[i] = a[j]; a[j] = t; }
+    }
+    __syncthreads();
+    for (int s = 1; s <= logM; ++s) {
+        const int half = 1 << (s - 1);
+        const int stride = Mmax >> s;
+        for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
+            const int pos = t & (half - 1);
+            const int i = ((t >> (s - 1)) << s) + pos;
+            const int j = i + half;
+            double2 w = __ldg(&tw[pos * stride]);
+            if (inverse) w.y = -w.y;
+            double2 u = a[i], v = cmul(a[j], w);
+            a[i] = cadd(u, v);
+            a[j] = csub(u, v);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_twiddle(double2 *tw, int Mmax) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Mmax / 2) return;
+    double s, c;
+    sincospi(2.0 * (double)t / (double)Mmax, &s, &c);
+    tw[t] = make_double2(c, -s);
+}
+
+__global__ void k_chirp(double2 *chirp, int L) {
+    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= (int64_t)L * L) return;
+    int k = (int)sqrt((double)j);
+    while ((int64_t)k * k > j) --k;
+    while ((int64_t)(k + 1) * (k + 1) <= j) ++k;
+    int64_t n = j - (int64_t)k * k, N = 2 * k + 1;
+    int64_t r = (n * n) % (2 * N);
+    double s, c;
+    sincospi((double)r / (double)N, &s, &c);
+    chirp[j] = make_double2(c, -s);  // e^{-i pi r / N}
+}
+
+// Filter of ring k: FFT_M of b_t = conj(c_t) (t < N), b_{M-t} = conj(c_t) (0 < t < N), scaled 1/M.
+__global__ void k_filter(int k0, const double2 *__restrict__ chirp, const int64_t *__restrict__ foff,
+                         const int *__restrict__ fM, const double2 *__restrict__ tw, int Mmax,
+                         double2 *__restrict__ filt) {
+    extern __shared__ double2 sa[];
+    const int k = k0 + blockIdx.x;
+    const int N = 2 * k + 1, M = fM[k];
+    int logM = 31 - __clz(M);
+    const double2 *c = chirp + (int64_t)k * k;
+    for (int t = threadIdx.x; t < M; t += blockDim.x) {
+        double2 v = make_double2(0.0, 0.0);
+        if (t < N) v = conjd(c[t]);
+        else if (t > M - N) v = conjd(c[M - t]);
+        sa[t] = v;
+    }
+    __syncthreads();
+    block_fft(sa, M, logM, tw, Mmax, false);
+    const double sc = 1.0 / (double)M;
+    for (int t = threadIdx.x; t < M; t += blockDim.x)
+        filt[foff[k] + t] = make_double2(sa[t].x * sc, sa[t].y * sc);
+}
+
+enum OutMode : int { OUT_BINS = 0, OUT_UNFOLD = 1 };
+enum InMode : int { IN_FOLD = 0, IN_BINS = 1 };
+
+struct DftArgs {
+    int L, k0;
+    int64_t Nc;             // 4 * batch columns of the order-major buffers
+    const double2 *chirp, *filt, *tw;
+    const int64_t *foff;
+    int Mmax, M, logM;
+};
+
+// Forward DFT of ring k = k0 + blockIdx.x of signal b = blockIdx.y.
+//  OUT_BINS:   W rows of bins +-q (scaled 1/N)           - forward transform
+//  OUT_UNFOLD: Gt rows (|m|, k) for every |m| < L, value of bin alias_k(m) (unscaled)
+//              - adjoint of fold_ring_idft
+template <int OUT>
+__global__ void k_ring_dft(DftArgs d, const double2 *__restrict__ samples, double *__restrict__ out) {
+    extern __shared__ double2 sa[];
+    const int k = d.k0 + blockIdx.x, b = blockIdx.y, L = d.L;
+    const int N = 2 * k + 1;
+    const double2 *x = samples + (int64_t)b * L * L + (int64_t)k * k;
+    double2 *X;  // natural-order DFT, N values
+    if (d.M == 0) {
+        double2 *xs = sa, *roots = sa + N;
+        X = sa + 2 * N;
+        for (int t = threadIdx.x; t < N; t += blockDim.x) {
+            xs[t] = x[t];
+            double s, c;
+            sincospi(2.0 * (double)t / (double)N, &s, &c);
+            roots[t] = make_double2(c, -s);
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            double2 acc = make_double2(0.0, 0.0);
+            int idx = 0;
+            for (int n = 0; n < N; ++n) {
+                double2 p = cmul(xs[n], roots[idx]);
+                acc.x += p.x; acc.y += p.y;
+                idx += j; if (idx >= N) idx -= N;
+            }
+            X[j] = acc;
+        }
+        __syncthreads();
+    } else {
+        const double2 *c = d.chirp + (int64_t)k * k;
+        const double2 *f = d.filt + d.foff[k];
+        for (int t = threadIdx.x; t < d.M; t += blockDim.x)
+            sa[t] = (t < N) ? cmul(x[t], c[t]) : make_double2(0.0, 0.0);
+        __syncthreads();
+        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, false);
+        for (int t = threadIdx.x; t < d.M; t += blockDim.x) sa[t] = cmul(sa[t], f[t]);
+        __syncthreads();
+        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, true);
+        for (int t = threadIdx.x; t < N; t += blockDim.x) sa[t] = cmul(c[t], sa[t]);
+        __syncthreads();
+        X = sa;
+    }
+    if (OUT == OUT_BINS) {
+        const double sc = 1.0 / (double)N;
+        for (int j = threadIdx.x; j < N; j += blockDim.x) {
+            const int q = (j <= k) ? j : j - N;
+            const int o = q < 0 ? -q : q;
+            double *w = out + (rows_off(L, o) + (k - o)) * d.Nc + 4 * b;
+            double2 v = X[j];
+            if (q >= 0) { w[0] = v.x * sc; w[1] = v.y * sc; }
+            else        { w[2] = v.x * sc; w[3] = v.y * sc; }
+            if (q == 0) { w[2] = 0.0; w[3] = 0.0; }
+        }
+    } else {
+        for (int m = -(L - 1) + (int)threadIdx.x; m <= L - 1; m += blockDim.x) {
+            int q = alias_bin(m, k);
+            int j = q >= 0 ? q : q + N;
+            int o = m < 0 ? -m : m;
+            double *g = out + ((int64_t)o * L + k) * d.Nc + 4 * b;
+            double2 v = X[j];
+            if (m >= 0) { g[0] = v.x; g[1] = v.y; }
+            else        { g[2] = v.x; g[3] = v.y; }
+            if (m == 0) { g[2] = 0.0; g[3] = 0.0; }
+        }
+    }
+}
+
+// Inverse DFT of ring k of signal b: gathers the ring's N bins, then s_n = sum_j B_j e^{+2 pi i jn/N}.
+//  IN_FOLD: B_q = sum_{m = q mod N, |m| < L} Gt[(|m|, k)]             - inverse transform
+//  IN_BINS: B_q = W[bin q of ring k] / N                              - adjoint of the forward DFT
+template <int IN>
+__global__ void k_ring_idft(DftArgs d, const double *__restrict__ in, double2 *__restrict__ samples) {
+    extern __shared__ double2 sa[];
+    const int k = d.k0 + blockIdx.x, b = blockIdx.y, L = d.L;
+    const int N = 2 * k + 1;
+    double2 *B = (d.M == 0) ? sa : sa;  // natural-order bins
+    for (int j = threadIdx.x; j < N; j += blockDim.x) {
+        const int q = (j <= k) ? j : j - N;
+        double2 acc = make_double2(0.0, 0.0);
+        if (IN == IN_FOLD) {
+            int m = q - ((q + L - 1) / N) * N;
+            for (; m <= L - 1; m += N) {
+                const int o = m < 0 ? -m : m;
+                const double *g = in + ((int64_t)o * L + k) * d.Nc + 4 * b + (m < 0 ? 2 : 0);
+                acc.x += g[0];
+                acc.y += g[1];
+            }
+        } else {
+            const int o = q < 0 ? -q : q;
+            const double *w = in + (rows_off(L, o) + (k - o)) * d.Nc + 4 * b + (q < 0 ? 2 : 0);
+            const double sc = 1.0 / (double)N;
+            acc = make_double2(w[0] * sc, w[1] * sc);
+        }
+        B[j] = acc;
+    }
+    __syncthreads();
+    double2 *y = samples + (int64_t)b * L * L + (int64_t)k * k;
+    if (d.M == 0) {
+        double2 *roots = sa + N;
+        for (int t = threadIdx.x; t < N; t += blockDim.x) {
+            double s, c;
+            sincospi(2.0 * (double)t / (double)N, &s, &c);
+            roots[t] = make_double2(c, s);  // e^{+2 pi i t / N}
+        }
+        __syncthreads();
+        for (int n = threadIdx.x; n < N; n += blockDim.x) {
+            double2 acc = make_double2(0.0, 0.0);
+            int idx = 0;
+            for (int j = 0; j < N; ++j) {
+                double2 p = cmul(B[j], roots[idx]);
+                acc.x += p.x; acc.y += p.y;
+                idx += n; if (idx >= N) idx -= N;
+            }
+            y[n] = acc;
+        }
+    } else {
+        // y = conj(DFT(conj(B))) with the forward chirp machinery
+        const double2 *c = d.chirp + (int64_t)k * k;
+        const double2 *f = d.filt + d.foff[k];
+        for (int t = threadIdx.x; t < d.M; t += blockDim.x)
+            sa[t] = (t < N) ? cmul(conjd(sa[t]), c[t]) : make_double2(0.0, 0.0);
+        __syncthreads();
+        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, false);
+        for (int t = threadIdx.x; t < d.M; t += blockDim.x) sa[t] = cmul(sa[t], f[t]);
+        __syncthreads();
+        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, true);
+        for (int t = threadIdx.x; t < N; t += blockDim.x) y[t] = conjd(cmul(c[t], sa[t]));
+    }
+}
+
+int ilog2(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
+
+// Ring classes: direct rings k < 32 (N <= 63), then k in [2^j, 2^(j+1)) with M = 2^(j+3).
+template <typename F>
+cudaError_t for_each_class(int L, F &&fn) {
+    int kd = L < 32 ? L : 32;
+    cudaError_t e = fn(0, kd, 0);
+    if (e != cudaSuccess) return e;
+    for (int j = 5; (1 << j) < L; ++j) {
+        int k0 = 1 << j, k1 = (1 << (j + 1)) < L ? (1 << (j + 1)) : L;
+        e = fn(k0, k1 - k0, 1 << (j + 3));
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+DftArgs make_args(int L, const DftPlan &dp, int64_t batch, int k0, int M) {
+    DftArgs d{};
+    d.L = L; d.k0 = k0; d.Nc = 4 * batch;
+    d.chirp = dp.chirp; d.filt = dp.filt; d.tw = dp.twiddle; d.foff = dp.filt_off;
+    d.Mmax = dp.Mmax; d.M = M; d.logM = M ? ilog2(M) : 0;
+    return d;
+}
+
+template <typename K>
+cudaError_t set_smem(K kernel, size_t bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+size_t smem_bytes(int k0, int cnt, int M) {
+    if (M == 0) { int N = 2 * (k0 + cnt - 1) + 1; return sizeof(double2) * 3 * (size_t)N; }
+    return sizeof(double2) * (size_t)M;
+}
+
+}  // namespace
+
+cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s) {
+    int Mmax = 2;
+    for (int j = 5; (1 << j) < L; ++j) Mmax = 1 << (j + 3);
+    dp.Mmax = Mmax;
+    dp.h_filt_off.assign(L, -1);
+    dp.h_filt_M.assign(L, 0);
+    int64_t total = 0;
+    for (int k = 32; k < L; ++k) {
+        int N = 2 * k + 1, M = 1 << ilog2(2 * N - 1);
+        dp.h_filt_off[k] = total;
+        dp.h_filt_M[k] = M;
+        total += M;
+    }
+    cudaError_t e;
+    size_t b_tw = sizeof(double2) * (Mmax / 2), b_ch = sizeof(double2) * (size_t)L * L;
+    size_t b_f = sizeof(double2) * (size_t)(total > 0 ? total : 1);
+    if ((e = cudaMalloc(&dp.twiddle, b_tw)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&dp.chirp, b_ch)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&dp.filt, b_f)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&dp.filt_off, sizeof(int64_t) * L)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&dp.filt_M, sizeof(int) * L)) != cudaSuccess) return e;
+    bytes = b_tw + b_ch + b_f + sizeof(int64_t) * L + sizeof(int) * L;
+    cudaMemcpyAsync(dp.filt_off, dp.h_filt_off.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(dp.filt_M, dp.h_filt_M.data(), sizeof(int) * L, cudaMemcpyHostToDevice, s);
+    k_twiddle<<<(Mmax / 2 + 255) / 256, 256, 0, s>>>(dp.twiddle, Mmax);
+    int64_t LL = (int64_t)L * L;
+    k_chirp<<<(unsigned)((LL + 255) / 256), 256, 0, s>>>(dp.chirp, L);
+    if (L > 32) {
+        if ((e = set_smem(k_filter, sizeof(double2) * Mmax)) != cudaSuccess) return e;
+        e = for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
+            if (M == 0 || cnt <= 0) return cudaSuccess;
+            k_filter<<<cnt, 256, sizeof(double2) * M, s>>>(k0, dp.chirp, dp.filt_off, dp.filt_M,
+                                                          dp.twiddle, Mmax, dp.filt);
+            return cudaGetLastError();
+        });
+        if (e != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+void dft_plan_destroy(DftPlan &dp) {
+    cudaFree(dp.twiddle); cudaFree(dp.chirp); cudaFree(dp.filt);
+    cudaFree(dp.filt_off); cudaFree(dp.filt_M);
+    dp = DftPlan{};
+}
+
+template <int OUT>
+static cudaError_t ring_dft_impl(int L, const DftPlan &dp, const double2 *samples, double *out,
+                                 int64_t batch, cudaStream_t s) {
+    return for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
+        if (cnt <= 0) return cudaSuccess;
+        size_t sm = smem_bytes(k0, cnt, M);
+        cudaError_t e = set_smem(k_ring_dft<OUT>, sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid(cnt, (unsigned)batch);
+        k_ring_dft<OUT><<<grid, M == 0 ? 64 : 256, sm, s>>>(make_args(L, dp, batch, k0, M), samples, out);
+        return cudaGetLastError();
+    });
+}
+
+template <int IN>
+static cudaError_t ring_idft_impl(int L, const DftPlan &dp, const double *in, double2 *samples,
+                                  int64_t batch, cudaStream_t s) {
+    return for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
+        if (cnt <= 0) return cudaSuccess;
+        size_t sm = smem_bytes(k0, cnt, M);
+        cudaError_t e = set_smem(k_ring_idft<IN>, sm);
+        if (e != cudaSuccess) return e;
+        dim3 grid(cnt, (unsigned)batch);
+        k_ring_idft<IN><<<grid, M == 0 ? 64 : 256, sm, s>>>(make_args(L, dp, batch, k0, M), in, samples);
+        return cudaGetLastError();
+    });
+}
+
+cudaError_t ring_dft_to_bins(int L, const DftPlan &dp, const double2 *samples, double *W,
+                             int64_t batch, bool, cudaStream_t s) {
+    return ring_dft_impl<OUT_BINS>(L, dp, samples, W, batch, s);
+}
+cudaError_t ring_dft_unfold(int L, const DftPlan &dp, const double2 *samples, double *Gt,
+                            int64_t batch, cudaStream_t s) {
+    return ring_dft_impl<OUT_UNFOLD>(L, dp, samples, Gt, batch, s);
+}
+cudaError_t fold_ring_idft(int L, const DftPlan &dp, const double *Gt, double2 *samples,
+                           int64_t batch, cudaStream_t s) {
+    return ring_idft_impl<IN_FOLD>(L, dp, Gt, samples, batch, s);
+}
+cudaError_t bins_to_ring_adjoint(int L, const DftPlan &dp, const double *W, double2 *samples,
+                                 int64_t batch, cudaStream_t s) {
+    return ring_idft_impl<IN_BINS>(L, dp, W, samples, batch, s);
+}
+
+}  // namespace sht

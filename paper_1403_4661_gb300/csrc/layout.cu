@@ -1,0 +1,94 @@
+// Coefficient layout <-> order-major layout.
+// Coefficients: f_l^m at l^2 + l + m (per signal).  Order-major block m >= 0: row l - m holds
+// (f_l^{+m}, (-1)^m f_l^{-m}) for every signal; the (-1)^m is Eq. (23) (P~^{-m} = (-1)^m P~^m)
+// moved onto the data so that one real table P~^m serves both signs of m.
+#include "sht_internal.cuh"
+
+namespace sht {
+namespace {
+
+__device__ __forceinline__ void decode(int64_t idx, int &l, int &m) {
+    int ll = (int)sqrt((double)idx);
+    while ((int64_t)ll * ll > idx) --ll;
+    while ((int64_t)(ll + 1) * (ll + 1) <= idx) ++ll;
+    l = ll;
+    m = (int)(idx - (int64_t)ll * ll - ll);
+}
+
+__global__ void k_coeffs_to_orders(int L, int64_t batch, const double2 *__restrict__ coeffs,
+                                   double *__restrict__ X) {
+    const int64_t L2 = (int64_t)L * L;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L2 * batch) return;
+    const int64_t b = t / L2, idx = t - b * L2;
+    int l, m;
+    decode(idx, l, m);
+    const int o = m < 0 ? -m : m;
+    double *x = X + (rows_off(L, o) + (l - o)) * (4 * batch) + 4 * b;
+    double2 v = coeffs[t];
+    if (m >= 0) {
+        x[0] = v.x; x[1] = v.y;
+        if (m == 0) { x[2] = 0.0; x[3] = 0.0; }
+    } else {
+        const double sg = (o & 1) ? -1.0 : 1.0;
+        x[2] = sg * v.x; x[3] = sg * v.y;
+    }
+}
+
+__global__ void k_orders_to_coeffs(int L, int64_t batch, const double *__restrict__ X,
+                                   double2 *__restrict__ coeffs) {
+    const int64_t L2 = (int64_t)L * L;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L2 * batch) return;
+    const int64_t b = t / L2, idx = t - b * L2;
+    int l, m;
+    decode(idx, l, m);
+    const int o = m < 0 ? -m : m;
+    const double *x = X + (rows_off(L, o) + (l - o)) * (4 * batch) + 4 * b;
+    if (m >= 0) {
+        coeffs[t] = make_double2(x[0], x[1]);
+    } else {
+        const double sg = (o & 1) ? -1.0 : 1.0;
+        coeffs[t] = make_double2(sg * x[2], sg * x[3]);
+    }
+}
+
+// U[k][4b + 2s + c], k < m: bin alias_k(+m) (s = 0) and alias_k(-m) (s = 1) of ring k, read from
+// the order-major bins W (bin q of ring k: block |q|, row k - |q|, slot 0 for q >= 0, 2 for q < 0).
+__global__ void k_gather_alias_bins(int L, int m, int64_t batch, const double *__restrict__ W,
+                                    double *__restrict__ U) {
+    const int64_t Nc = 4 * batch;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)m * batch) return;
+    const int k = (int)(t / batch), b = (int)(t - (int64_t)k * batch);
+    const int a = alias_bin(m, k);
+    const int o = a < 0 ? -a : a;
+    const double *w = W + (rows_off(L, o) + (k - o)) * Nc + 4 * b;
+    const int sp = a >= 0 ? 0 : 2, sn = a > 0 ? 2 : 0;  // slots of bins a and -a (bin 0: slot 0)
+    double *u = U + (int64_t)k * Nc + 4 * b;
+    u[0] = w[sp]; u[1] = w[sp + 1];
+    u[2] = w[sn]; u[3] = w[sn + 1];
+}
+
+}  // namespace
+
+cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U, cudaStream_t s) {
+    int64_t n = (int64_t)m * batch;
+    if (n <= 0) return cudaSuccess;
+    k_gather_alias_bins<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, m, batch, W, U);
+    return cudaGetLastError();
+}
+
+cudaError_t coeffs_to_orders(int L, int64_t batch, const double2 *coeffs, double *X, cudaStream_t s) {
+    int64_t n = (int64_t)L * L * batch;
+    k_coeffs_to_orders<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, coeffs, X);
+    return cudaGetLastError();
+}
+
+cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coeffs, cudaStream_t s) {
+    int64_t n = (int64_t)L * L * batch;
+    k_orders_to_coeffs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, X, coeffs);
+    return cudaGetLastError();
+}
+
+}  // namespace sht

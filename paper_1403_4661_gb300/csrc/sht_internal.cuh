@@ -1,0 +1,162 @@
+// Internal declarations of libsht (not part of the C ABI).
+//
+// Device data layouts (all float64; complex data interleaved re, im):
+//
+//  P~ table  pt      block m >= 0 at pt_off(L, m): L rows (ring k = 0..L-1, in theta order),
+//                    n_m = L - m columns (degree l = m..L-1); row-major.  P~_l^m(theta_k),
+//                    the functions of Sec. III-G evaluated at every ring.
+//  inverses  pinv    block m at pinv_off(L, m): n_m x n_m row-major, row l - m, column k - m:
+//                    (P_m)^{-1} with P_m[k][l] = P~_l^m(theta_k), k, l >= m (Eq. (12) without the
+//                    2 pi factor, which the project's scaling of G_m drops).
+//  order-major work  W, F, X   block m at rows_off(L, m) rows, n_m rows (k - m or l - m), each row
+//                    4B doubles: column 4b + 2s + c for signal b, s = 0 (+m) / 1 (-m), c = re/im.
+//                    In W (forward bins): row k holds bin +-m of ring k.  In F / X (coefficients):
+//                    row l holds f_l^{+m} and (-1)^m f_l^{-m}  (the sign folds Eq. (23) into the
+//                    data so that P~^{-m} never appears).
+//  synthesis G      Gt   row m * L + k (m >= 0, every ring k), 4B doubles, same column layout:
+//                    slot s = 0 holds G_{+m}(theta_k), slot s = 1 holds G_{-m}(theta_k).
+//
+// Scaling convention: G_m(theta_k) here is sum_l P~_l^m(theta_k) f_l^m (Eq. (11) without 2 pi),
+// ring DFTs carry 1/N_k, so that bin j of ring k equals sum_{m = j mod N_k} G_m(theta_k).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sht.h"
+
+namespace sht {
+
+__host__ __device__ inline int64_t pt_off(int64_t L, int64_t m) {
+    return L * (m * L - m * (m - 1) / 2);
+}
+__host__ __device__ inline int64_t sq_sum(int64_t n) { return n * (n + 1) * (2 * n + 1) / 6; }
+__host__ __device__ inline int64_t pinv_off(int64_t L, int64_t m) {
+    return sq_sum(L) - sq_sum(L - m);
+}
+__host__ __device__ inline int64_t rows_off(int64_t L, int64_t m) {
+    return m * L - m * (m - 1) / 2;
+}
+__host__ __device__ inline int64_t rows_total(int64_t L) { return L * (L + 1) / 2; }
+
+// Bin of ring k (length 2k+1) that order m aliases to, in [-k, k].
+__host__ __device__ inline int alias_bin(int m, int k) {
+    int N = 2 * k + 1;
+    int r = (m + k) % N;
+    if (r < 0) r += N;
+    return r - k;
+}
+
+// Rings whose DFT is taken directly (O(N^2)); longer rings use Bluestein's chirp-z transform.
+constexpr int kDirectMaxN = 63;
+
+struct DftPlan {
+    int Mmax = 0;                  // largest power-of-two convolution length
+    double2 *chirp = nullptr;      // e^{-i pi n^2 / N_k}, n < N_k, ring k at offset k^2
+    double2 *filt = nullptr;       // per Bluestein ring: FFT_M of the conjugate chirp, scaled
+    int64_t *filt_off = nullptr;   // device, per ring (-1 for direct rings)
+    int *filt_M = nullptr;         // device, per ring convolution length (0 for direct rings)
+    double2 *twiddle = nullptr;    // e^{-2 pi i t / Mmax}, t < Mmax / 2
+    std::vector<int64_t> h_filt_off;
+    std::vector<int> h_filt_M;
+};
+
+}  // namespace sht
+
+struct sht_plan_s {
+    int L = 0;
+    int dtype = 0;
+    int device = 0;
+    std::vector<double> theta;
+    double *d_theta = nullptr;
+    double *pt = nullptr;       // P~ table
+    double *pinv = nullptr;     // per-order inverses
+    sht::DftPlan dft;
+    // workspaces
+    int64_t ws_batch = 0;
+    double *ws_a = nullptr;     // W (forward bins) / X (inverse coefficients): rows_total * 4B
+    double *ws_b = nullptr;     // F (forward solved coefficients): rows_total * 4B
+    double *ws_g = nullptr;     // Gt (inverse synthesis): L * L * 4B
+    uint64_t table_bytes = 0;
+    uint64_t ws_bytes = 0;
+    double plan_seconds = 0.0;
+    double order_seconds = 0.0;
+    int64_t launches = 0;
+    // stage timing (sht_plan_set_timing)
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> spans[SHT_NUM_STAGES];
+};
+
+namespace sht {
+
+// error reporting (api.cu)
+sht_status set_error(sht_status st, const std::string &msg);
+sht_status cuda_check(cudaError_t e, const char *what);
+
+// legendre.cu: P~ table for arbitrary co-latitudes (rows), all orders.
+cudaError_t build_ptilde_table(int L, const double *d_theta_rows, int nrows, double *d_table,
+                               cudaStream_t s);
+// Table layout for nrows != L: block m at nrows * rows_off(L, m), nrows x n_m.
+
+// invert.cu: explicit inverses of P_m for every m from the P~ table.
+cudaError_t build_inverses(int L, const double *d_pt, double *d_pinv, cudaStream_t s);
+
+// dft.cu
+cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s);
+void dft_plan_destroy(DftPlan &dp);
+// forward ring DFTs of every ring of every signal, 1/N scaled, into the order-major bins W
+cudaError_t ring_dft_to_bins(int L, const DftPlan &dp, const double2 *samples, double *W,
+                             int64_t batch, bool scale, cudaStream_t s);
+// fold of the synthesis table into ring bins + inverse ring DFTs
+cudaError_t fold_ring_idft(int L, const DftPlan &dp, const double *Gt, double2 *samples,
+                           int64_t batch, cudaStream_t s);
+// adjoint of ring_dft_to_bins (scale = 1/N): bins -> samples
+cudaError_t bins_to_ring_adjoint(int L, const DftPlan &dp, const double *W, double2 *samples,
+                                 int64_t batch, cudaStream_t s);
+// adjoint of fold_ring_idft: samples -> unfolded synthesis table Gt
+cudaError_t ring_dft_unfold(int L, const DftPlan &dp, const double2 *samples, double *Gt,
+                            int64_t batch, cudaStream_t s);
+
+// gemm_f64.cu
+enum Epilogue : int {
+    EPI_STORE = 0,       // C = A B
+    EPI_SOLVE = 1,       // C = A B, and coefficients of order m written to the output
+    EPI_ALIAS = 2,       // rows k < m: W[alias bins] -= A B
+    EPI_ADJ_SOLVE = 3,   // adjoint chain: W bins of order m (rows k >= m) = A^T B
+    EPI_SUB = 4,         // C = C0 - A B (C0 given)
+};
+struct GemmArgs {
+    int L;
+    int64_t batch;
+    int m;                 // order of this problem (single-problem launches)
+    double2 *coeffs;       // EPI_SOLVE output
+    double *W;             // EPI_ALIAS target
+};
+// Single problem: C[M x N] (+)= op(A)[M x K] * B[K x N], row-major, N = 4 * batch.
+cudaError_t gemm_f64(bool transA, int M, int K, int N, const double *A, int64_t lda,
+                     const double *B, int64_t ldb, double *C, int64_t ldc, int epi,
+                     const GemmArgs &ga, cudaStream_t s, const double *C0 = nullptr);
+// Grouped over every order m: Gt[m][k][:] = P~[m][k][:] . X[m] (all k), or the transposed
+// contraction for the adjoint (out[m][l][:] = sum_k P~[m][k][l] U[m][k][:]).
+cudaError_t synthesis_all_orders(int L, int64_t batch, const double *pt, const double *X,
+                                 double *Gt, cudaStream_t s);
+cudaError_t analysis_all_orders(int L, int64_t batch, const double *pt, const double *U,
+                                double *X, cudaStream_t s);
+
+// layout.cu: coefficient <-> order-major conversions
+cudaError_t coeffs_to_orders(int L, int64_t batch, const double2 *coeffs, double *X,
+                             cudaStream_t s);
+cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coeffs,
+                             cudaStream_t s);
+// adjoint chain: U[k] (k < m) = the bins of ring k that orders +m / -m alias to
+cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U,
+                              cudaStream_t s);
+
+// planner.cu: greedy condition-number ordering (indices into the equiangular set)
+sht_status greedy_order(int L, std::vector<int> &order);
+
+}  // namespace sht

@@ -1,0 +1,289 @@
+"""Thin Python binding of libsht (include/sht.h): argument marshalling only.
+
+Every step of the transforms runs in the CUDA library; this module passes device pointers of
+torch tensors and the current CUDA stream through the C ABI.  There is no fallback: if
+libsht.so is missing or fails to load, the first call raises.
+
+Functions with the C names (``sht_plan``, ``sht_forward``, ...) mirror the ABI one to one; the
+``Plan`` class wraps a plan handle, and ``SHTForward`` / ``SHTInverse`` are the
+``torch.autograd.Function``s whose backward passes call the adjoint entry points (PyTorch's
+complex convention: grad_input = M^H grad_output for a linear map M).
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsht.so")
+
+SHT_OK = 0
+SHT_STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3: "SHT_ERR_OOM",
+              4: "SHT_ERR_CUDA", 5: "SHT_ERR_NOT_CONVERGED", 6: "SHT_ERR_TIMEOUT"}
+SHT_F64 = 0
+SHT_ORDER_GREEDY = 0
+SHT_ORDER_SIMPLE = 1
+EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
+            "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
+            "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
+            "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times"]
+STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
+
+
+class SHTError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{SHT_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ShtInfo(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("dtype", ctypes.c_int), ("table_bytes", ctypes.c_uint64),
+                ("workspace_bytes", ctypes.c_uint64), ("workspace_batch", ctypes.c_int64),
+                ("plan_seconds", ctypes.c_double), ("order_seconds", ctypes.c_double),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libsht.so (once) and declare the ABI's signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsht.so not found at {path}; build it with "
+                           "`python -m paper_1403_4661_gb300.build` (there is no CPU fallback)")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i64 = ctypes.c_int64
+    lib.sht_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(P)]
+    lib.sht_plan_with_thetas.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_uint32, ctypes.POINTER(P)]
+    lib.sht_plan_thetas.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.sht_plan_bandlimit.argtypes = [P]
+    lib.sht_plan_bandlimit.restype = ctypes.c_int
+    lib.sht_plan_reserve.argtypes = [P, i64]
+    lib.sht_plan_destroy.argtypes = [P]
+    for name in ("sht_forward", "sht_inverse", "sht_inverse_adjoint", "sht_forward_adjoint"):
+        getattr(lib, name).argtypes = [P, P, P, i64, P]
+    lib.sht_get_info.argtypes = [P, ctypes.POINTER(ShtInfo)]
+    lib.sht_status_string.argtypes = [ctypes.c_int]
+    lib.sht_status_string.restype = ctypes.c_char_p
+    lib.sht_plan_set_timing.argtypes = [P, ctypes.c_int]
+    lib.sht_plan_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+    lib.sht_last_error_message.argtypes = []
+    lib.sht_last_error_message.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("sht_plan_bandlimit", "sht_status_string", "sht_last_error_message"):
+            getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status):
+    if status != SHT_OK:
+        msg = _lib.sht_last_error_message().decode(errors="replace")
+        raise SHTError(status, msg)
+
+
+def _stream_ptr(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# -------------------------------------------------------------------------------------------
+# C-named wrappers
+# -------------------------------------------------------------------------------------------
+
+def sht_plan(L, dtype=SHT_F64, flags=SHT_ORDER_GREEDY):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.sht_plan(int(L), int(dtype), int(flags), ctypes.byref(h)))
+    return h
+
+
+def sht_plan_with_thetas(L, theta, dtype=SHT_F64, flags=0):
+    lib = load_library()
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    if th.shape != (L,):
+        raise ValueError("theta must have L entries")
+    h = ctypes.c_void_p()
+    _check(lib.sht_plan_with_thetas(int(L), int(dtype),
+                                    th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    int(flags), ctypes.byref(h)))
+    return h
+
+
+def sht_plan_thetas(h, L):
+    out = np.zeros(L, dtype=np.float64)
+    _check(load_library().sht_plan_thetas(h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+    return out
+
+
+def sht_plan_destroy(h):
+    _check(load_library().sht_plan_destroy(h))
+
+
+def sht_plan_reserve(h, batch):
+    _check(load_library().sht_plan_reserve(h, int(batch)))
+
+
+def sht_get_info(h):
+    info = ShtInfo()
+    _check(load_library().sht_get_info(h, ctypes.byref(info)))
+    return {f: getattr(info, f) for f, _ in ShtInfo._fields_}
+
+
+def sht_plan_set_timing(h, enable):
+    _check(load_library().sht_plan_set_timing(h, 1 if enable else 0))
+
+
+def sht_plan_stage_times(h):
+    """{stage: (milliseconds, spans)} summed since the last query; clears the record."""
+    ms = (ctypes.c_double * len(STAGES))()
+    n = (ctypes.c_int64 * len(STAGES))()
+    _check(load_library().sht_plan_stage_times(h, ms, n))
+    return {name: (ms[i], n[i]) for i, name in enumerate(STAGES)}
+
+
+def _call(name, h, inp, out, batch, stream=None):
+    fn = getattr(load_library(), name)
+    _check(fn(h, ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(out.data_ptr()), int(batch),
+              _stream_ptr(stream)))
+
+
+def _as_batch(x, L, name):
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != torch.complex128:
+        raise TypeError(f"{name} must be complex128")
+    if x.shape[-1] != L * L:
+        raise ValueError(f"{name}: last dimension must be L^2 = {L * L}")
+    return x.contiguous()
+
+
+def sht_forward(h, L, samples, out=None, stream=None):
+    x = _as_batch(samples, L, "samples")
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_forward", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+def sht_inverse(h, L, coeffs, out=None, stream=None):
+    x = _as_batch(coeffs, L, "coeffs")
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_inverse", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+def sht_forward_adjoint(h, L, coeffs, out=None, stream=None):
+    x = _as_batch(coeffs, L, "coeffs")
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_forward_adjoint", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+def sht_inverse_adjoint(h, L, samples, out=None, stream=None):
+    x = _as_batch(samples, L, "samples")
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_inverse_adjoint", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+# -------------------------------------------------------------------------------------------
+# Plan object and autograd
+# -------------------------------------------------------------------------------------------
+
+class Plan:
+    """A libsht plan for band-limit L on the current CUDA device.
+
+    Plan(L)                           greedy condition-number ring ordering (Sec. III-E)
+    Plan(L, ordering="simple")        the ordering of Eq. (20)
+    Plan(L, theta=array_of_L_values)  caller-given ring co-latitudes
+    """
+
+    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64):
+        self.L = int(L)
+        if theta is not None:
+            self.handle = sht_plan_with_thetas(self.L, theta, dtype)
+        else:
+            flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering]
+            self.handle = sht_plan(self.L, dtype, flags)
+        self.theta = sht_plan_thetas(self.handle, self.L)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None:
+            sht_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, batch):
+        sht_plan_reserve(self.handle, batch)
+
+    def info(self):
+        return sht_get_info(self.handle)
+
+    def set_timing(self, enable=True):
+        sht_plan_set_timing(self.handle, enable)
+
+    def stage_times(self):
+        return sht_plan_stage_times(self.handle)
+
+    def forward(self, samples, out=None, stream=None):
+        return sht_forward(self.handle, self.L, samples, out, stream)
+
+    def inverse(self, coeffs, out=None, stream=None):
+        return sht_inverse(self.handle, self.L, coeffs, out, stream)
+
+    def forward_adjoint(self, coeffs, out=None, stream=None):
+        return sht_forward_adjoint(self.handle, self.L, coeffs, out, stream)
+
+    def inverse_adjoint(self, samples, out=None, stream=None):
+        return sht_inverse_adjoint(self.handle, self.L, samples, out, stream)
+
+
+class SHTForward(torch.autograd.Function):
+    """coeffs = F(samples); backward: grad_samples = F^H grad_coeffs."""
+
+    @staticmethod
+    def forward(ctx, plan, samples):
+        ctx.plan = plan
+        return plan.forward(samples)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return None, ctx.plan.forward_adjoint(grad.contiguous())
+
+
+class SHTInverse(torch.autograd.Function):
+    """samples = A(coeffs); backward: grad_coeffs = A^H grad_samples."""
+
+    @staticmethod
+    def forward(ctx, plan, coeffs):
+        ctx.plan = plan
+        return plan.inverse(coeffs)
+
+    @staticmethod
+    def backward(ctx, grad):
+        return None, ctx.plan.inverse_adjoint(grad.contiguous())
+
+
+def forward(plan, samples):
+    """Differentiable forward SHT; real input is promoted to complex128."""
+    if not samples.is_complex():
+        samples = samples.to(torch.complex128)
+    return SHTForward.apply(plan, samples)
+
+
+def inverse(plan, coeffs):
+    """Differentiable inverse SHT."""
+    if not coeffs.is_complex():
+        coeffs = coeffs.to(torch.complex128)
+    return SHTInverse.apply(plan, coeffs)

@@ -1,0 +1,166 @@
+"""CUDA path vs the oracle, through the C ABI (libsht.so), on seeded synthetic inputs.
+
+Tolerances: coefficients (forward outputs) 1e-11 absolute, the float64 target; samples (inverse
+outputs) 1e-11 relative to the largest sample.  Sizes span the direct / chirp-z ring boundary
+(k = 31 / 32), the 32- and 64-wide GEMM tiles with ragged tails, and batches > 1.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sht as osht
+from paper_1403_4661_gb300 import synth
+from tests.helpers import oracle_thetas, tol_samples
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1403_4661_gb300 import build
+    build.build()
+
+
+def _plan(L):
+    from paper_1403_4661_gb300.sht import Plan
+    return Plan(L, theta=oracle_thetas(L))
+
+
+def _gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+SIZES = [(1, 1), (2, 2), (3, 1), (8, 3), (31, 2), (32, 1), (33, 2), (64, 1), (65, 3), (100, 2), (130, 1)]
+
+
+@pytest.mark.parametrize("L,B", SIZES)
+def test_inverse_matches_oracle(L, B):
+    th = oracle_thetas(L)
+    c = synth.uniform_coeffs(L, B, 100 + L)
+    ref = osht.inverse(c, L, th)
+    p = _plan(L)
+    got = p.inverse(_gpu(c)).cpu().numpy()
+    assert np.abs(got - ref).max() <= tol_samples(ref)
+
+
+@pytest.mark.parametrize("L,B", SIZES)
+def test_forward_matches_oracle(L, B):
+    th = oracle_thetas(L)
+    s = synth.uniform_samples(L, B, 200 + L)
+    ref = osht.forward(s, L, th)
+    p = _plan(L)
+    got = p.forward(_gpu(s)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-11
+
+
+def test_config1_round_trip_L64():
+    """One complex signal, L = 64, f_lm re/im U[-1,1], samples made by the oracle's inverse."""
+    L = 64
+    th = oracle_thetas(L)
+    c = synth.uniform_coeffs(L, 1, 0)
+    s = osht.inverse(c, L, th)
+    p = _plan(L)
+    got = p.forward(_gpu(s)).cpu().numpy()
+    assert np.abs(got - osht.forward(s, L, th)).max() <= 1e-11
+    assert np.abs(got - c).max() <= 1e-11
+    s2 = p.inverse(_gpu(got)).cpu().numpy()
+    assert np.abs(s2 - s).max() <= tol_samples(s)
+
+
+@pytest.mark.parametrize("L", [8, 16, 33, 64, 128])
+def test_library_greedy_ordering_matches_oracle(L):
+    from paper_1403_4661_gb300.sht import Plan
+    p = Plan(L)  # library planner on the GPU
+    np.testing.assert_allclose(p.theta, oracle_thetas(L), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("L,B", [(512, 256), (1024, 64)])
+def test_full_size_sampled(L, B):
+    """Full-size batches in the bench's launch configuration; sampled outputs vs the oracle."""
+    th = oracle_thetas(L)
+    c = synth.decaying_coeffs(L, B, 7)
+    p = _plan(L)
+    cg = _gpu(c)
+    s = p.inverse(cg)
+    c2 = p.forward(s)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(L)
+    idx = np.sort(rng.choice(L * L, 24, replace=False))
+    idx[0], idx[-1] = 0, L * L - 1
+    sig = [0, B // 2, B - 1]
+    s_h = s[sig].cpu().numpy()
+    ref = osht.evaluate_samples(c[sig], L, th, idx)
+    assert np.abs(s_h[:, idx] - ref).max() <= tol_samples(s_h)
+    # forward: Exp. 1 round trip for every signal, and A(forward(s)) = s at the sampled points
+    err = (c2 - cg).abs().max().item()
+    assert err <= 1e-11, err
+    c2_h = c2[sig[:1]].cpu().numpy()
+    ref2 = osht.evaluate_samples(c2_h, L, th, idx)
+    assert np.abs(ref2 - s_h[:1, idx]).max() <= tol_samples(s_h)
+
+
+def test_round_trip_exp2_L256():
+    L, B = 256, 4
+    p = _plan(L)
+    s = _gpu(synth.uniform_samples(L, B, 9))
+    s2 = p.inverse(p.forward(s))
+    assert (s2 - s).abs().max().item() <= 1e-11 * s.abs().max().item() * 10
+
+
+@pytest.mark.parametrize("L", [5, 33, 64])
+def test_inverse_adjoint_matches_oracle(L):
+    th = oracle_thetas(L)
+    y = synth.uniform_samples(L, 2, 300 + L)
+    ref = osht.inverse_adjoint(y, L, th)
+    got = _plan(L).inverse_adjoint(_gpu(y)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("L", [3, 8, 12])
+def test_forward_adjoint_matches_dense_oracle(L):
+    th = oracle_thetas(L)
+    A = osht.dense_matrix(L, th)
+    w = synth.normal_coeffs(L, 2, 400 + L)
+    ref = osht.dense_forward_adjoint(w, A)
+    got = _plan(L).forward_adjoint(_gpu(w)).cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("L", [64, 256])
+def test_adjoint_dot_products(L):
+    p = _plan(L)
+    x = _gpu(synth.uniform_samples(L, 2, 1))
+    y = _gpu(synth.normal_coeffs(L, 2, 2))
+    for fwd, adj, a, b in ((p.forward, p.forward_adjoint, x, y), (p.inverse, p.inverse_adjoint, y, x)):
+        lhs = torch.vdot(b.flatten(), fwd(a).flatten())
+        rhs = torch.vdot(adj(b).flatten(), a.flatten())
+        assert abs(lhs - rhs).item() <= 1e-12 * abs(lhs).item()
+
+
+def test_batch_zero_and_bad_arguments():
+    from paper_1403_4661_gb300 import sht as S
+    L = 8
+    p = _plan(L)
+    x = _gpu(synth.uniform_samples(L, 2, 3))
+    lib = S.load_library()
+    import ctypes
+    h = p.handle
+    assert lib.sht_forward(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr() + 16 * 64), 0, None) == 0
+    # overlapping in/out
+    assert lib.sht_forward(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr() + 16), 1, None) == 1
+    # misaligned
+    assert lib.sht_inverse(h, ctypes.c_void_p(x.data_ptr() + 8), ctypes.c_void_p(x.data_ptr() + 16 * 64 + 16), 1, None) == 1
+    assert lib.sht_forward(h, None, ctypes.c_void_p(x.data_ptr()), 1, None) == 1
+    assert lib.sht_forward(h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr() + 16 * 64), 70000, None) == 1
+
+
+def test_deterministic():
+    L = 100
+    p = _plan(L)
+    s = _gpu(synth.uniform_samples(L, 3, 4))
+    a, b = p.forward(s), p.forward(s)
+    assert torch.equal(a, b)
+    c = p.inverse(a)
+    assert torch.equal(c, p.inverse(a))
