@@ -33,8 +33,8 @@ constexpr int kMaxL = 2048;           // longest ring 4095 -> Bluestein length 8
 constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring kernels
 
 void free_workspaces(sht_plan_t p) {
-    cudaFree(p->ws_a); cudaFree(p->ws_b); cudaFree(p->ws_g);
-    p->ws_a = p->ws_b = p->ws_g = nullptr;
+    cudaFree(p->ws_a); cudaFree(p->ws_b); cudaFree(p->ws_g); cudaFree(p->ws_part);
+    p->ws_a = p->ws_b = p->ws_g = p->ws_part = nullptr;
     p->ws_batch = 0;
     p->ws_bytes = 0;
 }
@@ -60,15 +60,17 @@ sht_status ensure_workspace(sht_plan_t p, int64_t batch) {
     const size_t L = (size_t)p->L;
     const size_t a = sizeof(double) * (size_t)rows_total(p->L) * 4 * (size_t)batch;
     const size_t g = sizeof(double) * L * L * 4 * (size_t)batch;
+    const size_t sp = sizeof(double) * (size_t)kSplitCap * L * 4 * (size_t)batch;
     cudaError_t e = cudaMalloc(&p->ws_a, a);
     if (e == cudaSuccess) e = cudaMalloc(&p->ws_b, a);
     if (e == cudaSuccess) e = cudaMalloc(&p->ws_g, g);
+    if (e == cudaSuccess) e = cudaMalloc(&p->ws_part, sp);
     if (e != cudaSuccess) {
         free_workspaces(p);
         return cuda_check(e, "workspace allocation");
     }
     p->ws_batch = batch;
-    p->ws_bytes = 2 * a + g;
+    p->ws_bytes = 2 * a + g + sp;
     return SHT_OK;
 }
 
@@ -311,6 +313,8 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
     }
     GemmArgs ga{};
     ga.L = L; ga.batch = batch; ga.coeffs = (double2 *)d_coeffs; ga.W = W;
+    ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.launches = &p->launches;
     for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
         const int n = L - m;
         ga.m = m;
@@ -325,7 +329,7 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
                          nullptr, Nc, EPI_ALIAS, ga, s);
         }
     }
-    p->launches += ring_launches(L) + 2 * L - 1;
+    p->launches += ring_launches(L);
     return cuda_check(e, "sht_forward");
 }
 
@@ -393,6 +397,8 @@ sht_status sht_forward_adjoint(sht_plan_t p, const void *d_coeffs, void *d_sampl
     }
     GemmArgs ga{};
     ga.L = L; ga.batch = batch;
+    ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.launches = &p->launches;
     // reverse of the forward chain: m = 0 .. L-1
     for (int m = 0; m < L && e == cudaSuccess; ++m) {
         const int n = L - m;
@@ -415,7 +421,7 @@ sht_status sht_forward_adjoint(sht_plan_t p, const void *d_coeffs, void *d_sampl
         Span sp(p, SHT_STAGE_RING_IDFT, s);
         e = bins_to_ring_adjoint(L, p->dft, W, (double2 *)d_samples, batch, s);
     }
-    p->launches += 1 + L + 2 * (L - 1) + ring_launches(L);
+    p->launches += 1 + (L - 1) + ring_launches(L);  // layout, alias gathers, ring DFTs
     return cuda_check(e, "sht_forward_adjoint");
 }
 

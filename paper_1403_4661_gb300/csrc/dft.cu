@@ -271,6 +271,17 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Raise the dynamic shared-memory limit of the ring kernels once, at plan time, so that the
+// transform calls themselves make no attribute calls (they may run under stream capture).
+cudaError_t set_ring_kernel_limits(int Mmax) {
+    const size_t b = sizeof(double2) * (size_t)Mmax;
+    cudaError_t e;
+    if ((e = set_smem(k_ring_dft<OUT_BINS>, b)) != cudaSuccess) return e;
+    if ((e = set_smem(k_ring_dft<OUT_UNFOLD>, b)) != cudaSuccess) return e;
+    if ((e = set_smem(k_ring_idft<IN_FOLD>, b)) != cudaSuccess) return e;
+    return set_smem(k_ring_idft<IN_BINS>, b);
+}
+
 size_t smem_bytes(int k0, int cnt, int M) {
     if (M == 0) { int N = 2 * (k0 + cnt - 1) + 1; return sizeof(double2) * 3 * (size_t)N; }
     return sizeof(double2) * (size_t)M;
@@ -305,6 +316,7 @@ cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s)
     k_twiddle<<<(Mmax / 2 + 255) / 256, 256, 0, s>>>(dp.twiddle, Mmax);
     int64_t LL = (int64_t)L * L;
     k_chirp<<<(unsigned)((LL + 255) / 256), 256, 0, s>>>(dp.chirp, L);
+    if ((e = set_ring_kernel_limits(Mmax)) != cudaSuccess) return e;
     if (L > 32) {
         if ((e = set_smem(k_filter, sizeof(double2) * Mmax)) != cudaSuccess) return e;
         e = for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
@@ -330,8 +342,6 @@ static cudaError_t ring_dft_impl(int L, const DftPlan &dp, const double2 *sample
     return for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
         if (cnt <= 0) return cudaSuccess;
         size_t sm = smem_bytes(k0, cnt, M);
-        cudaError_t e = set_smem(k_ring_dft<OUT>, sm);
-        if (e != cudaSuccess) return e;
         dim3 grid(cnt, (unsigned)batch);
         k_ring_dft<OUT><<<grid, M == 0 ? 64 : 256, sm, s>>>(make_args(L, dp, batch, k0, M), samples, out);
         return cudaGetLastError();
@@ -344,8 +354,6 @@ static cudaError_t ring_idft_impl(int L, const DftPlan &dp, const double *in, do
     return for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
         if (cnt <= 0) return cudaSuccess;
         size_t sm = smem_bytes(k0, cnt, M);
-        cudaError_t e = set_smem(k_ring_idft<IN>, sm);
-        if (e != cudaSuccess) return e;
         dim3 grid(cnt, (unsigned)batch);
         k_ring_idft<IN><<<grid, M == 0 ? 64 : 256, sm, s>>>(make_args(L, dp, batch, k0, M), in, samples);
         return cudaGetLastError();

@@ -8,12 +8,16 @@
 //  analysis   the transposed contraction (adjoint of synthesis)
 //  solve      F_m = P_m^{-1} W_m  (Eq. (14)), writing f_l^{+-m} to the coefficient output
 //  alias      G_{+-m}(theta_k), k < m, subtracted from bin alias_k(+-m) of ring k (Eqs. (15)-(16))
+#include <algorithm>
+
 #include "sht_internal.cuh"
 
 namespace sht {
 namespace {
 
 constexpr int BK = 16;
+constexpr int kSMs = 152;
+constexpr int kMaxSplit = 16;
 
 enum Mode : int { MODE_SINGLE = 0, MODE_SYNTH = 1, MODE_ANALYSIS = 2 };
 
@@ -28,17 +32,73 @@ struct Params {
     double2 *coeffs; // EPI_SOLVE
     double *W;       // EPI_ALIAS
     const double *pt; const double *X; double *Y;  // grouped modes
+    double *part;    // split-K partial sums [split][M][N]
+    int splits, kchunk;
 };
 
 // sum_{j=1..x} ceil(j / bm)
-__device__ __forceinline__ int64_t ceil_sum(int64_t x, int64_t bm) {
+__host__ __device__ __forceinline__ int64_t ceil_sum(int64_t x, int64_t bm) {
     int64_t q = x / bm, r = x % bm;
     return bm * q * (q + 1) / 2 + r * (q + 1);
 }
 
-template <int BM, int BN, bool TA, int EPI, int MODE>
-__global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_gemm(Params p) {
-    constexpr int NT = (BM / 4) * (BN / 4);
+// One output row r and the four columns c0..c0+3 of one signal: (+m re, +m im, -m re, -m im).
+template <int EPI>
+__device__ __forceinline__ void epilogue(const Params &p, double *C, int64_t ldc, int m, int N,
+                                         int r, int c0, const double v[4]) {
+    if (EPI == EPI_STORE || EPI == EPI_SOLVE) {
+        double *cr = C + (int64_t)r * ldc + c0;
+        if (c0 + 4 <= N && (ldc & 1) == 0) {
+            *reinterpret_cast<double2 *>(cr) = make_double2(v[0], v[1]);
+            *reinterpret_cast<double2 *>(cr + 2) = make_double2(v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c0 + j < N) cr[j] = v[j];
+        }
+    }
+    if (EPI == EPI_SUB) {
+        const double *c0r = p.C0 + (int64_t)r * ldc + c0;
+        double *cr = C + (int64_t)r * ldc + c0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cr[j] = c0r[j] - v[j];
+    }
+    if (EPI == EPI_SOLVE) {
+        // row r is degree l = m + r; columns (b, +m re/im, -m re/im)
+        const int64_t L2 = (int64_t)p.L * p.L;
+        const int l = m + r, b = c0 >> 2;
+        double2 *cb = p.coeffs + (int64_t)b * L2 + (int64_t)l * l + l;
+        cb[m] = make_double2(v[0], v[1]);
+        if (m > 0) {
+            const double sg = (m & 1) ? -1.0 : 1.0;   // f_l^{-m} = (-1)^m F_l^{-}
+            cb[-m] = make_double2(sg * v[2], sg * v[3]);
+        }
+    }
+    if (EPI == EPI_ALIAS) {
+        // row r is ring k = r < m; subtract G_{+m}, G_{-m} from bins a, -a of ring k
+        const int k = r, b = c0 >> 2;
+        const int a = alias_bin(m, k);
+        const int o = a < 0 ? -a : a;
+        double *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
+        if (a == 0) {
+            w[0] -= v[0] + v[2];
+            w[1] -= v[1] + v[3];
+        } else {
+            const int sp = a > 0 ? 0 : 2;   // slot of bin a  (+o or -o)
+            const int sm = 2 - sp;          // slot of bin -a
+            w[sp] -= v[0];
+            w[sp + 1] -= v[1];
+            w[sm] -= v[2];
+            w[sm + 1] -= v[3];
+        }
+    }
+}
+
+// Tile BM x BN, each thread TM rows x 4 columns (one signal), K in steps of BK through shared
+// memory.  SPLIT: blockIdx.y selects a K chunk and the raw partial sums go to p.part.
+template <int BM, int BN, int TM, bool TA, int EPI, int MODE, bool SPLIT>
+__global__ void __launch_bounds__((BM / TM) * (BN / 4)) k_gemm(Params p) {
+    constexpr int NT = (BM / TM) * (BN / 4);
     __shared__ __align__(16) double As[BK][BM + 2];
     __shared__ __align__(16) double Bs[BK][BN + 2];
 
@@ -77,41 +137,53 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_gemm(Params p) {
         C = p.Y + rows_off(p.L, m) * N; ldc = N;
         M = n; K = p.L;
     }
+    int kbeg = 0, kend = K;
+    if (SPLIT) {
+        kbeg = blockIdx.y * p.kchunk;
+        kend = min(K, kbeg + p.kchunk);
+    }
     const int tm = (int)(tile / tiles_n), tn = (int)(tile % tiles_n);
     const int row0 = tm * BM, col0 = tn * BN;
     const int tx = threadIdx.x % (BN / 4), ty = threadIdx.x / (BN / 4);
 
-    double acc[4][4];
+    double acc[TM][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < TM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-    for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
         for (int idx = threadIdx.x; idx < BM * BK; idx += NT) {
             int i, kk;
             if (!TA) { i = idx / BK; kk = idx % BK; } else { kk = idx / BM; i = idx % BM; }
             int r = row0 + i, k = k0 + kk;
             double v = 0.0;
-            if (r < M && k < K) v = TA ? A[(int64_t)k * lda + r] : A[(int64_t)r * lda + k];
+            if (r < M && k < kend) v = TA ? A[(int64_t)k * lda + r] : A[(int64_t)r * lda + k];
             As[kk][i] = v;
         }
         for (int idx = threadIdx.x; idx < BN * BK; idx += NT) {
             int kk = idx / BN, j = idx % BN;
             int k = k0 + kk, c = col0 + j;
-            Bs[kk][j] = (k < K && c < N) ? B[(int64_t)k * ldb + c] : 0.0;
+            Bs[kk][j] = (k < kend && c < N) ? B[(int64_t)k * ldb + c] : 0.0;
         }
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double2 a01 = *reinterpret_cast<const double2 *>(&As[kk][ty * 4]);
-            double2 a23 = *reinterpret_cast<const double2 *>(&As[kk][ty * 4 + 2]);
+            double a[TM];
+            if (TM == 1) {
+                a[0] = As[kk][ty];
+            } else {
+#pragma unroll
+                for (int i = 0; i < TM; i += 2) {
+                    double2 t = *reinterpret_cast<const double2 *>(&As[kk][ty * TM + i]);
+                    a[i] = t.x; a[i + 1] = t.y;
+                }
+            }
             double2 b01 = *reinterpret_cast<const double2 *>(&Bs[kk][tx * 4]);
             double2 b23 = *reinterpret_cast<const double2 *>(&Bs[kk][tx * 4 + 2]);
-            double a[4] = {a01.x, a01.y, a23.x, a23.y};
             double b[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TM; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
@@ -121,72 +193,86 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) k_gemm(Params p) {
     const int c0 = col0 + tx * 4;
     if (c0 >= N) return;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = row0 + ty * 4 + i;
+    for (int i = 0; i < TM; ++i) {
+        const int r = row0 + ty * TM + i;
         if (r >= M) break;
-        if (EPI == EPI_STORE || EPI == EPI_SOLVE) {
-            double *cr = C + (int64_t)r * ldc + c0;
-            if (c0 + 4 <= N && (ldc & 1) == 0) {
-                *reinterpret_cast<double2 *>(cr) = make_double2(acc[i][0], acc[i][1]);
-                *reinterpret_cast<double2 *>(cr + 2) = make_double2(acc[i][2], acc[i][3]);
-            } else {
+        if (SPLIT) {
+            double *pp = p.part + ((int64_t)blockIdx.y * M + r) * N + c0;
 #pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (c0 + j < N) cr[j] = acc[i][j];
-            }
-        }
-        if (EPI == EPI_SUB) {
-            const double *c0r = p.C0 + (int64_t)r * ldc + c0;
-            double *cr = C + (int64_t)r * ldc + c0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) cr[j] = c0r[j] - acc[i][j];
-        }
-        if (EPI == EPI_SOLVE) {
-            // row r is degree l = m + r; columns (b, +m re/im, -m re/im)
-            const int64_t L2 = (int64_t)p.L * p.L;
-            const int l = m + r, b = c0 >> 2;
-            double2 *cb = p.coeffs + (int64_t)b * L2 + (int64_t)l * l + l;
-            cb[m] = make_double2(acc[i][0], acc[i][1]);
-            if (m > 0) {
-                const double sg = (m & 1) ? -1.0 : 1.0;   // f_l^{-m} = (-1)^m F_l^{-}
-                cb[-m] = make_double2(sg * acc[i][2], sg * acc[i][3]);
-            }
-        }
-        if (EPI == EPI_ALIAS) {
-            // row r is ring k = r < m; subtract G_{+m}, G_{-m} from bins a, -a of ring k
-            const int k = r, b = c0 >> 2;
-            const int a = alias_bin(m, k);
-            const int o = a < 0 ? -a : a;
-            double *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
-            if (a == 0) {
-                w[0] -= acc[i][0] + acc[i][2];
-                w[1] -= acc[i][1] + acc[i][3];
-            } else {
-                const int sp = a > 0 ? 0 : 2;   // slot of bin a  (+o or -o)
-                const int sm = 2 - sp;          // slot of bin -a
-                w[sp] -= acc[i][0];
-                w[sp + 1] -= acc[i][1];
-                w[sm] -= acc[i][2];
-                w[sm + 1] -= acc[i][3];
-            }
+            for (int j = 0; j < 4; ++j)
+                if (c0 + j < N) pp[j] = acc[i][j];
+        } else {
+            epilogue<EPI>(p, C, ldc, m, N, r, c0, acc[i]);
         }
     }
 }
 
-constexpr int kSMs = 152;
+// Sum of the split-K partials in a fixed order (deterministic), then the epilogue.
+template <int EPI>
+__global__ void k_split_reduce(Params p) {
+    const int groups = (p.N + 3) / 4;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)p.M * groups) return;
+    const int r = (int)(t / groups), c0 = 4 * (int)(t - (int64_t)r * groups);
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int s = 0; s < p.splits; ++s) {
+        const double *pp = p.part + ((int64_t)s * p.M + r) * p.N + c0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (c0 + j < p.N) v[j] += pp[j];
+    }
+    epilogue<EPI>(p, p.C, p.ldc, p.m, p.N, r, c0, v);
+}
 
-template <bool TA, int EPI, int MODE>
-cudaError_t launch(const Params &p, int64_t tiles64, int64_t tiles32, cudaStream_t s) {
-    // 64x64 tiles (256 threads) when they alone give >= 2 waves of 152 SMs, else 32x32 (64 threads)
-    if (tiles64 >= 2 * kSMs) {
-        k_gemm<64, 64, TA, EPI, MODE><<<(unsigned)tiles64, 256, 0, s>>>(p);
+inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+struct Cfg { int bm, bn; };
+
+// Tile choice: enough blocks for >= 2 per SM when the problem allows, each block 8 warps so
+// that all four FP64 units of an SM are fed.
+template <bool TA, int EPI, int MODE, bool SPLIT>
+cudaError_t launch_cfg(const Params &p, Cfg c, dim3 grid, cudaStream_t s) {
+    if (c.bn == 64) {
+        if (c.bm == 64) k_gemm<64, 64, 4, TA, EPI, MODE, SPLIT><<<grid, 256, 0, s>>>(p);
+        else if (c.bm == 32) k_gemm<32, 64, 2, TA, EPI, MODE, SPLIT><<<grid, 256, 0, s>>>(p);
+        else k_gemm<16, 64, 1, TA, EPI, MODE, SPLIT><<<grid, 256, 0, s>>>(p);
     } else {
-        k_gemm<32, 32, TA, EPI, MODE><<<(unsigned)tiles32, 64, 0, s>>>(p);
+        k_gemm<16, 16, 1, TA, EPI, MODE, SPLIT><<<grid, 64, 0, s>>>(p);
     }
     return cudaGetLastError();
 }
 
-inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int64_t tiles_of(int M, int N, Cfg c) { return cdiv(M, c.bm) * cdiv(N, c.bn); }
+
+template <bool TA, int EPI>
+cudaError_t launch_single(Params p, cudaStream_t s, double *part, int64_t part_cap, int64_t *count) {
+    Cfg c{64, 64};
+    if (p.N <= 32) {
+        c = Cfg{16, 16};
+    } else {
+        for (int bm : {64, 32, 16}) {
+            c = Cfg{bm, 64};
+            if (tiles_of(p.M, p.N, c) >= 2 * kSMs) break;
+        }
+    }
+    const int64_t tiles = tiles_of(p.M, p.N, c);
+    int splits = 1;
+    if (part && tiles < 2 * kSMs && p.K >= 128) {
+        splits = (int)std::min<int64_t>(std::min<int64_t>(cdiv(2 * kSMs, tiles), p.K / 64), kMaxSplit);
+        while (splits > 1 && (int64_t)splits * p.M * p.N > part_cap) --splits;
+    }
+    if (count) *count += splits <= 1 ? 1 : 2;
+    if (splits <= 1) return launch_cfg<TA, EPI, MODE_SINGLE, false>(p, c, dim3((unsigned)tiles), s);
+    p.splits = splits;
+    p.kchunk = (int)(cdiv(cdiv(p.K, splits), BK) * BK);
+    p.splits = (int)cdiv(p.K, p.kchunk);
+    p.part = part;
+    cudaError_t e = launch_cfg<TA, EPI, MODE_SINGLE, true>(p, c, dim3((unsigned)tiles, p.splits), s);
+    if (e != cudaSuccess) return e;
+    const int64_t work = (int64_t)p.M * cdiv(p.N, 4);
+    k_split_reduce<EPI><<<(unsigned)cdiv(work, 256), 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
@@ -197,10 +283,9 @@ cudaError_t gemm_f64(bool transA, int M, int K, int N, const double *A, int64_t 
     Params p{};
     p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc; p.C0 = C0;
     p.M = M; p.K = K; p.N = N; p.m = ga.m; p.L = ga.L; p.coeffs = ga.coeffs; p.W = ga.W;
-    int64_t t64 = cdiv(M, 64) * cdiv(N, 64), t32 = cdiv(M, 32) * cdiv(N, 32);
 #define SHT_GEMM_CASE(E)                                                                  \
-    if (epi == E) return transA ? launch<true, E, MODE_SINGLE>(p, t64, t32, s)            \
-                                : launch<false, E, MODE_SINGLE>(p, t64, t32, s);
+    if (epi == E) return transA ? launch_single<true, E>(p, s, ga.part, ga.part_cap, ga.launches) \
+                                : launch_single<false, E>(p, s, ga.part, ga.part_cap, ga.launches);
     SHT_GEMM_CASE(EPI_STORE)
     SHT_GEMM_CASE(EPI_SOLVE)
     SHT_GEMM_CASE(EPI_ALIAS)
@@ -213,22 +298,18 @@ cudaError_t synthesis_all_orders(int L, int64_t batch, const double *pt, const d
                                  double *Gt, cudaStream_t s) {
     Params p{};
     p.L = L; p.N = (int)(4 * batch); p.pt = pt; p.X = X; p.Y = Gt;
-    int64_t t64 = (int64_t)L * cdiv(L, 64) * cdiv(p.N, 64);
-    int64_t t32 = (int64_t)L * cdiv(L, 32) * cdiv(p.N, 32);
-    return launch<false, EPI_STORE, MODE_SYNTH>(p, t64, t32, s);
+    Cfg c = p.N <= 32 ? Cfg{16, 16} : Cfg{64, 64};
+    const int64_t tiles = (int64_t)L * cdiv(L, c.bm) * cdiv(p.N, c.bn);
+    return launch_cfg<false, EPI_STORE, MODE_SYNTH, false>(p, c, dim3((unsigned)tiles), s);
 }
 
 cudaError_t analysis_all_orders(int L, int64_t batch, const double *pt, const double *U,
                                 double *X, cudaStream_t s) {
     Params p{};
     p.L = L; p.N = (int)(4 * batch); p.pt = pt; p.X = U; p.Y = X;
-    auto csum = [](int64_t x, int64_t bm) {
-        int64_t q = x / bm, r = x % bm;
-        return bm * q * (q + 1) / 2 + r * (q + 1);
-    };
-    int64_t t64 = cdiv(p.N, 64) * csum(L, 64);
-    int64_t t32 = cdiv(p.N, 32) * csum(L, 32);
-    return launch<true, EPI_STORE, MODE_ANALYSIS>(p, t64, t32, s);
+    Cfg c = p.N <= 32 ? Cfg{16, 16} : Cfg{64, 64};
+    const int64_t tiles = cdiv(p.N, c.bn) * ceil_sum(L, c.bm);
+    return launch_cfg<true, EPI_STORE, MODE_ANALYSIS, false>(p, c, dim3((unsigned)tiles), s);
 }
 
 }  // namespace sht

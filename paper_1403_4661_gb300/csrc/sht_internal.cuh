@@ -50,6 +50,9 @@ __host__ __device__ inline int alias_bin(int m, int k) {
     return r - k;
 }
 
+// Split-K partial buffer of the order chain holds this many L x 4B slices.
+constexpr int kSplitCap = 16;
+
 // Rings whose DFT is taken directly (O(N^2)); longer rings use Bluestein's chirp-z transform.
 constexpr int kDirectMaxN = 63;
 
@@ -80,6 +83,7 @@ struct sht_plan_s {
     double *ws_a = nullptr;     // W (forward bins) / X (inverse coefficients): rows_total * 4B
     double *ws_b = nullptr;     // F (forward solved coefficients): rows_total * 4B
     double *ws_g = nullptr;     // Gt (inverse synthesis): L * L * 4B
+    double *ws_part = nullptr;  // split-K partials of the order chain: kSplitCap * L * 4B
     uint64_t table_bytes = 0;
     uint64_t ws_bytes = 0;
     double plan_seconds = 0.0;
@@ -135,6 +139,9 @@ struct GemmArgs {
     int m;                 // order of this problem (single-problem launches)
     double2 *coeffs;       // EPI_SOLVE output
     double *W;             // EPI_ALIAS target
+    double *part = nullptr;  // split-K partial sums (none: no split)
+    int64_t part_cap = 0;    // doubles available at part
+    int64_t *launches = nullptr;  // incremented by the number of kernels launched
 };
 // Single problem: C[M x N] (+)= op(A)[M x K] * B[K x N], row-major, N = 4 * batch.
 cudaError_t gemm_f64(bool transA, int M, int K, int N, const double *A, int64_t lda,

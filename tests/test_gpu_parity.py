@@ -164,3 +164,29 @@ def test_deterministic():
     assert torch.equal(a, b)
     c = p.inverse(a)
     assert torch.equal(c, p.inverse(a))
+
+
+def test_graph_capture_replays_identically():
+    """The transforms allocate nothing and synchronise nothing once reserved, so a step of
+    inverse + forward can be captured in a CUDA graph and replayed."""
+    L, B = 100, 3
+    p = _plan(L)
+    p.reserve(B)
+    c = _gpu(synth.uniform_coeffs(L, B, 12))
+    s = torch.empty_like(c)
+    c2 = torch.empty_like(c)
+    p.inverse(c, out=s)
+    p.forward(s, out=c2)
+    ref = c2.clone()
+    c2.zero_()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            p.inverse(c, out=s)
+            p.forward(s, out=c2)
+    torch.cuda.current_stream().wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(c2, ref)
