@@ -27,7 +27,8 @@ SHT_ORDER_SIMPLE = 1
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
             "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
-            "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times"]
+            "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
+            "sht_forward_noalloc"]
 STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
 
 
@@ -66,7 +67,8 @@ def load_library(path=LIB_PATH):
     lib.sht_plan_bandlimit.restype = ctypes.c_int
     lib.sht_plan_reserve.argtypes = [P, i64]
     lib.sht_plan_destroy.argtypes = [P]
-    for name in ("sht_forward", "sht_inverse", "sht_inverse_adjoint", "sht_forward_adjoint"):
+    for name in ("sht_forward", "sht_inverse", "sht_inverse_adjoint", "sht_forward_adjoint",
+                 "sht_forward_noalloc"):
         getattr(lib, name).argtypes = [P, P, P, i64, P]
     lib.sht_get_info.argtypes = [P, ctypes.POINTER(ShtInfo)]
     lib.sht_status_string.argtypes = [ctypes.c_int]
@@ -168,6 +170,14 @@ def sht_forward(h, L, samples, out=None, stream=None):
     x = _as_batch(samples, L, "samples")
     y = torch.empty_like(x) if out is None else out
     _call("sht_forward", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+def sht_forward_noalloc(h, L, samples, out=None, stream=None):
+    """sht_forward with its scratch in the library's fixed device array (no allocation)."""
+    x = _as_batch(samples, L, "samples")
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_forward_noalloc", h, x, y, x.numel() // (L * L), stream)
     return y
 
 
