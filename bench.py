@@ -172,10 +172,14 @@ def run_reference(args):
 
 
 def _config(args):
+    arith = {"f64": "plain float64",
+             "f64_tensor": "float64-accurate, contractions on the BF16 tensor cores from exact slices"}
     return {"workload": f"{args.batch} complex signals at L={args.L}, f_lm re/im iid N(0,1)/(l+1); "
-                        "inverse SHT then forward SHT, plain float64",
+                        f"inverse SHT then forward SHT, {arith.get(getattr(args, 'dtype', 'f64'))}",
+            "arithmetic": getattr(args, "dtype", "f64"),
             "L": args.L, "batch_per_gpu": args.batch, "ordering": "greedy (Sec. III-E)",
-            "l2": "inputs larger than L2 (16 L^2 B bytes per buffer), no flush"}
+            "l2": "inputs larger than L2 (16 L^2 B bytes per buffer), no flush",
+            "launch": "one CUDA graph per step" if not getattr(args, "no_graph", False) else "eager"}
 
 
 def run_ours(args):
@@ -203,7 +207,7 @@ def run_ours(args):
                          "orders are the cheap ones: this overstates the oracle's speed ~1.5x)"}
 
     t0 = time.time()
-    plan = Plan(L)  # greedy ring ordering on the GPU, tables, per-order inverses
+    plan = Plan(L, dtype=args.dtype)  # greedy ring ordering on the GPU, tables, per-order inverses
     plan_s = time.time() - t0
     plan.reserve(B)
     c_host = torch.from_numpy(synth.decaying_coeffs(L, B, 1000 + rank)).pin_memory()
@@ -212,18 +216,40 @@ def run_ours(args):
     c2 = torch.empty_like(c)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def eager_step():
         plan.inverse(c, out=s)
         plan.forward(s, out=c2)
 
     for _ in range(args.warmup):
-        step()
+        eager_step()
     torch.cuda.synchronize()
     err = (c2 - c).abs().max().item()
+    step = eager_step
+    graph = None
+    if not args.no_graph:
+        # one CUDA graph per step: the library allocates nothing and makes no attribute or
+        # synchronising call once its workspaces are reserved, so the whole step is capturable
+        plan.set_timing(True)      # the stage event pairs are captured as graph nodes
+        plan.stage_times()
+        launches_after_capture0 = plan.info()["kernel_launches"]
+        graph = torch.cuda.CUDAGraph()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(graph):
+                eager_step()
+        torch.cuda.current_stream().wait_stream(side)
+        plan.set_timing(False)
+        captured_launches = plan.info()["kernel_launches"] - launches_after_capture0
+        step = graph.replay
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
 
     # ---- device-resident timed region --------------------------------------------------------
-    plan.set_timing(True)
-    plan.stage_times()
+    if graph is None:
+        plan.set_timing(True)
+        plan.stage_times()
     launches0 = plan.info()["kernel_launches"]
     clocks = ClockSampler(local)
     clocks.start()
@@ -242,9 +268,16 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
-    launches = plan.info()["kernel_launches"] - launches0
-    stages = plan.stage_times()
-    plan.set_timing(False)
+    if graph is None:
+        launches = plan.info()["kernel_launches"] - launches0
+        stages = plan.stage_times()
+        plan.set_timing(False)
+        stage_steps = args.steps
+    else:
+        # the graph's event pairs hold the spans of its last replay (the last timed step)
+        launches = captured_launches * args.steps
+        stages = plan.stage_times()
+        stage_steps = 1
     if dist is not None:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -255,8 +288,7 @@ def run_ours(args):
 
     def step_e2e():
         c.copy_(c_host, non_blocking=True)
-        plan.inverse(c, out=s)
-        plan.forward(s, out=c2)
+        step()
         out_host.copy_(c2, non_blocking=True)
 
     step_e2e()
@@ -279,23 +311,39 @@ def run_ours(args):
     if rank != 0:
         return
     # ---- roofline of the dominant kernel: the synthesis contraction (one launch per inverse) --
-    syn_ms, syn_n = stages["synthesis"]
+    syn_ms, syn_n = stages["synthesis"]          # summed ms over syn_n launches
     flops = 4.0 * B * L * L * (L + 1)     # sum_m 2 * L * (L - m) * 4B real multiply-adds
-    achieved = flops / (syn_ms / syn_n * 1e-3) / 1e12
+    sec = syn_ms / syn_n * 1e-3
     sm_mhz = (clk or {}).get("sm_mhz") or FP64_NOMINAL_MHZ
-    peak = FP64_TFLOPS_NOMINAL
-    roof = {"bound": "alu", "kernel": "k_gemm<64,64,false,EPI_STORE,MODE_SYNTH> (float64 synthesis, Eq. (11))",
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "peak_source": "GB300 float64 pipe, 1.25 TFLOP/s at 2070 MHz (DESIGN.md); at the measured "
-                           f"median {sm_mhz:.0f} MHz the clock-scaled peak is {peak * sm_mhz / FP64_NOMINAL_MHZ:.3f}",
-            "traffic": _traffic_record("synthesis_f64", L, B),
-            "stage_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
-            "stage_launch_spans_per_step": {k: v[1] / args.steps for k, v in stages.items()}}
+    peaks = _peaks()
+    if args.dtype == "f64_tensor":
+        # 36 BF16 slice-pair products per float64 product (8 slices a side, s + t <= 9)
+        achieved = 36.0 * flops / sec / 1e12
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        roof = {"bound": "tensor",
+                "kernel": "k_tc_gemm<EPI_STORE,grouped> (synthesis, Eq. (11), tcgen05 BF16 slices)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks.get(
+                    "bf16_tflops_sustained") else "fallback 1.7 PFLOP/s sustained bf16",
+                "fp64_equivalent_tflops": flops / sec / 1e12,
+                "traffic": _traffic_record("synthesis_tc", L, B)}
+    else:
+        achieved = flops / sec / 1e12
+        peak = FP64_TFLOPS_NOMINAL
+        roof = {"bound": "alu",
+                "kernel": "k_gemm<64,64,4,0,0,1,0> (float64 synthesis, Eq. (11))",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": "GB300 float64 pipe, 1.25 TFLOP/s at 2070 MHz (DESIGN.md); at the measured "
+                               f"median {sm_mhz:.0f} MHz the clock-scaled peak is {peak * sm_mhz / FP64_NOMINAL_MHZ:.3f}",
+                "traffic": _traffic_record("synthesis_f64", L, B)}
+    roof["stage_ms_per_step"] = {k: v[0] / stage_steps for k, v in stages.items()}
+    roof["stage_launch_spans_per_step"] = {k: v[1] / stage_steps for k, v in stages.items()}
     value = ws * B / (ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.dtype == "f64" else "f64 (bf16 tensor-core slices)",
+        "data": "synthetic",
         "config": dict(_config(args), parallelism=f"dp{ws}" if ws > 1 else "single GPU"),
         "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e},
         "roofline": roof,
@@ -318,6 +366,8 @@ def main():
     ap.add_argument("--L", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--dtype", default="f64_tensor", choices=["f64", "f64_tensor"])
+    ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of one CUDA graph per step")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

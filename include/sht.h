@@ -48,9 +48,20 @@ typedef enum {
     SHT_ERR_TIMEOUT = 6
 } sht_status;
 
-/* Arithmetic of the transforms.  SHT_F64: every step in float64 (FP64 pipe). */
+/*
+ * Arithmetic of the transforms.
+ *   SHT_F64         every step in float64 on the FP64 pipe.
+ *   SHT_F64_TENSOR  float64-accurate results; the Legendre contractions (synthesis, per-order
+ *                   solves, alias products) run on the BF16 tensor cores on exact 7-bit slices of
+ *                   the float64 operands (8 slices per operand, 36 slice-pair products, exact FP32
+ *                   accumulation of the leading diagonals, int64 folding), the ring DFTs and the
+ *                   Legendre recursion stay in float64.  Errors are of the order of a float64
+ *                   contraction.  The plan additionally holds the slices of its tables (about
+ *                   2x the float64 tables).  The adjoints run the float64 kernels.
+ */
 typedef enum {
-    SHT_F64 = 0
+    SHT_F64 = 0,
+    SHT_F64_TENSOR = 1
 } sht_dtype;
 
 /* Plan flags: ring ordering (Sec. III-E). */
@@ -75,8 +86,8 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out);
 
 /*
  * sht_plan_with_thetas - as sht_plan, with the L ring co-latitudes given by the caller (host
- *   array of L doubles, theta_host[k] = theta_k in radians, any values in [0, pi] for which every
- *   P_m is invertible; Remark 1).  The ordering bits of `flags` are ignored.
+ *   array of L doubles, theta_host[k] = theta_k in radians, any values in [0, pi] (to within
+ *   1e-12) for which every P_m is invertible; Remark 1).  The ordering bits of `flags` are ignored.
  */
 sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host, uint32_t flags,
                                 sht_plan_t *out);
@@ -154,6 +165,13 @@ sht_status sht_forward_adjoint(sht_plan_t plan, const void *d_coeffs, void *d_sa
  */
 sht_status sht_forward_noalloc(sht_plan_t plan, const void *d_samples, void *d_coeffs,
                                int64_t batch, void *stream);
+
+/*
+ * sht_plan_check - wait for the plan's queued work (synchronises the device) and report whether a
+ *   bounded wait inside a tensor-core kernel gave up since the last check (SHT_ERR_TIMEOUT; the
+ *   results of the affected call are then invalid).  Clears the flag.
+ */
+sht_status sht_plan_check(sht_plan_t plan);
 
 /* Plan information. */
 typedef struct {

@@ -35,6 +35,9 @@ constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring k
 void free_workspaces(sht_plan_t p) {
     cudaFree(p->ws_a); cudaFree(p->ws_b); cudaFree(p->ws_g); cudaFree(p->ws_part);
     p->ws_a = p->ws_b = p->ws_g = p->ws_part = nullptr;
+    cudaFree(p->ws_xS); cudaFree(p->ws_wS); cudaFree(p->ws_xE); cudaFree(p->ws_wE);
+    p->ws_xS = p->ws_wS = nullptr;
+    p->ws_xE = p->ws_wE = nullptr;
     p->ws_batch = 0;
     p->ws_bytes = 0;
 }
@@ -45,6 +48,8 @@ void destroy(sht_plan_t p) {
     cudaGetDevice(&dev);
     if (dev != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_theta); cudaFree(p->pt); cudaFree(p->pinv);
+    cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
+    cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status);
     dft_plan_destroy(p->dft);
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -71,7 +76,52 @@ sht_status ensure_workspace(sht_plan_t p, int64_t batch) {
     }
     p->ws_batch = batch;
     p->ws_bytes = 2 * a + g + sp;
+    if (p->dtype == SHT_F64_TENSOR) {
+        const size_t Nc = 4 * (size_t)batch;
+        const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
+        const size_t ws = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)((p->L + 7) & ~7);
+        e = cudaMalloc(&p->ws_xS, xs);
+        if (e == cudaSuccess) e = cudaMalloc(&p->ws_xE, sizeof(int) * Nc * (size_t)p->L);
+        if (e == cudaSuccess) e = cudaMalloc(&p->ws_wS, ws);
+        if (e == cudaSuccess) e = cudaMalloc(&p->ws_wE, sizeof(int) * Nc);
+        if (e != cudaSuccess) {
+            free_workspaces(p);
+            return cuda_check(e, "workspace allocation");
+        }
+        p->ws_bytes += xs + ws + sizeof(int) * Nc * ((size_t)p->L + 1);
+    }
     return SHT_OK;
+}
+
+// Slices of the P~ table and of the per-order inverses for SHT_F64_TENSOR plans.
+sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
+    const int L = p->L;
+    p->ptk_off.assign(L + 1, 0);
+    p->pik_off.assign(L + 1, 0);
+    for (int m = 0; m < L; ++m) {
+        const int64_t n = L - m, kp = (n + 7) & ~7;
+        p->ptk_off[m + 1] = p->ptk_off[m] + kp;
+        p->pik_off[m + 1] = p->pik_off[m] + n * kp;
+    }
+    const size_t pts = sizeof(__nv_bfloat16) * kTcSlices * (size_t)L * (size_t)p->ptk_off[L];
+    const size_t pis = sizeof(__nv_bfloat16) * kTcSlices * (size_t)p->pik_off[L];
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->ptS, pts)) != cudaSuccess ||
+        (e = cudaMalloc(&p->piS, pis)) != cudaSuccess ||
+        (e = cudaMalloc(&p->ptE, sizeof(int) * (size_t)L * L)) != cudaSuccess ||
+        (e = cudaMalloc(&p->piE, sizeof(int) * (size_t)rows_total(L))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_ptk_off, sizeof(int64_t) * (L + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&p->d_pik_off, sizeof(int64_t) * (L + 1))) != cudaSuccess)
+        return cuda_check(e, "tensor-core table allocation");
+    bytes = pts + pis + sizeof(int) * ((size_t)L * L + rows_total(L)) + 2 * sizeof(int64_t) * (L + 1);
+    cudaMemcpyAsync(p->d_ptk_off, p->ptk_off.data(), sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->d_pik_off, p->pik_off.data(), sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice, s);
+    if ((e = tc_prepare_kernels()) != cudaSuccess) return cuda_check(e, "tensor-core kernel attributes");
+    if ((e = tc_slice_table(p->pt, L, false, p->d_ptk_off, p->ptS, p->ptE, s)) != cudaSuccess ||
+        (e = tc_slice_table(p->pinv, L, true, p->d_pik_off, p->piS, p->piE, s)) != cudaSuccess)
+        return cuda_check(e, "tensor-core table slices");
+    e = cudaStreamSynchronize(s);
+    return cuda_check(e, "tensor-core table slices");
 }
 
 sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, double order_s,
@@ -113,9 +163,16 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_check(e, "ring DFT plan");
     }
+    uint64_t tc_bytes = 0;
+    if (st == SHT_OK) {
+        e = cudaMalloc(&p->d_status, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e != cudaSuccess) st = cuda_check(e, "status word");
+    }
+    if (st == SHT_OK && dtype == SHT_F64_TENSOR) st = build_tensor_tables(p, s, tc_bytes);
     cudaStreamDestroy(s);
     if (st != SHT_OK) { destroy(p); *out = nullptr; return st; }
-    p->table_bytes = pt_bytes + pi_bytes + dft_bytes + sizeof(double) * L;
+    p->table_bytes = pt_bytes + pi_bytes + dft_bytes + tc_bytes + sizeof(double) * L;
     p->plan_seconds = order_s + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
     return SHT_OK;
@@ -145,13 +202,14 @@ struct Span {
     int stage;
     cudaStream_t s;
     cudaEvent_t b = nullptr;
+    // "external" records stay real event records when the stream is being captured into a graph
     Span(sht_plan_t p_, int stage_, cudaStream_t s_) : p(p_), stage(stage_), s(s_) {
-        if (p->timing) { b = take_event(p); cudaEventRecord(b, s); }
+        if (p->timing) { b = take_event(p); cudaEventRecordWithFlags(b, s, cudaEventRecordExternal); }
     }
     ~Span() {
         if (p->timing) {
             cudaEvent_t e = take_event(p);
-            cudaEventRecord(e, s);
+            cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
             p->spans[stage].push_back({b, e});
         }
     }
@@ -205,11 +263,12 @@ sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if (dtype != SHT_F64) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if (dtype != SHT_F64 && dtype != SHT_F64_TENSOR) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     if (!theta_host) return set_error(SHT_ERR_INVALID_ARG, "theta_host is NULL");
     std::vector<double> th(theta_host, theta_host + L);
+    // the equiangular set's end point pi (2L-1)/(2L-1) may round one ulp past pi: allow 1e-12
     for (double t : th)
-        if (!(t >= 0.0 && t <= M_PI)) return set_error(SHT_ERR_INVALID_ARG, "theta outside [0, pi]");
+        if (!(t >= -1e-12 && t <= M_PI + 1e-12)) return set_error(SHT_ERR_INVALID_ARG, "theta outside [0, pi]");
     return build_plan(L, dtype, th, 0.0, out);
 }
 
@@ -217,7 +276,7 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if (dtype != SHT_F64) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if (dtype != SHT_F64 && dtype != SHT_F64_TENSOR) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     std::vector<int> order(L);
     auto t0 = std::chrono::steady_clock::now();
     if ((flags & SHT_ORDER_MASK) == SHT_ORDER_SIMPLE) {
@@ -270,6 +329,17 @@ sht_status sht_get_info(sht_plan_t p, sht_info *out) {
     return SHT_OK;
 }
 
+sht_status sht_plan_check(sht_plan_t p) {
+    if (!p) return set_error(SHT_ERR_INVALID_ARG, "plan is NULL");
+    int h = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(p->d_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(e, "sht_plan_check");
+    if (h) return set_error(SHT_ERR_TIMEOUT, "a bounded wait in a tensor-core kernel gave up");
+    return SHT_OK;
+}
+
 sht_status sht_plan_set_timing(sht_plan_t p, int enable) {
     if (!p) return set_error(SHT_ERR_INVALID_ARG, "plan is NULL");
     p->timing = enable != 0;
@@ -311,6 +381,37 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
         Span sp(p, SHT_STAGE_RING_DFT, s);
         e = ring_dft_to_bins(L, p->dft, (const double2 *)d_samples, W, batch, true, s);
     }
+    if (p->dtype == SHT_F64_TENSOR) {
+        const int64_t cap = (int64_t)kSplitCap * L * Nc;
+        for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
+            const int n = L - m, kp = (n + 7) & ~7;
+            const TcOperand bins{p->ws_wS, p->ws_wE, Nc * kp, kp};
+            {   // Eq. (14) on the tensor cores: slices of g_m, then F_m = P_m^{-1} g_m
+                Span sp(p, SHT_STAGE_SOLVE, s);
+                e = tc_slice_cols(W + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
+                const TcOperand inv{p->piS + (int64_t)kTcSlices * p->pik_off[m], p->piE + rows_off(L, m),
+                                    (int64_t)n * kp, kp};
+                const TcEpilogue ep{F + rows_off(L, m) * Nc, Nc, nullptr, m, L, (double2 *)d_coeffs, nullptr};
+                if (e == cudaSuccess)
+                    e = tc_gemm(inv, bins, n, (int)Nc, n, EPI_SOLVE, ep, p->d_status, s, p->ws_part, cap,
+                                &p->launches);
+                p->launches += 1;
+            }
+            if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): rings k < m
+                Span sp(p, SHT_STAGE_ALIAS, s);
+                e = tc_slice_cols(F + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
+                const TcOperand low{p->ptS + (int64_t)kTcSlices * L * p->ptk_off[m], p->ptE + (int64_t)m * L,
+                                    (int64_t)L * kp, kp};
+                const TcEpilogue ep{nullptr, Nc, nullptr, m, L, nullptr, W};
+                if (e == cudaSuccess)
+                    e = tc_gemm(low, bins, m, (int)Nc, n, EPI_ALIAS, ep, p->d_status, s, p->ws_part, cap,
+                                &p->launches);
+                p->launches += 1;
+            }
+        }
+        p->launches += ring_launches(L);
+        return cuda_check(e, "sht_forward");
+    }
     GemmArgs ga{};
     ga.L = L; ga.batch = batch; ga.coeffs = (double2 *)d_coeffs; ga.W = W;
     ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
@@ -347,7 +448,15 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     }
     if (e == cudaSuccess) {  // Eq. (11): G_{+-m}(theta_k) for every order and ring
         Span sp(p, SHT_STAGE_SYNTHESIS, s);
-        e = synthesis_all_orders(L, batch, p->pt, p->ws_a, p->ws_g, s);
+        if (p->dtype == SHT_F64_TENSOR) {
+            e = tc_slice_orders(p->ws_a, L, batch, p->d_ptk_off, p->ws_xS, p->ws_xE, s);
+            if (e == cudaSuccess)
+                e = tc_synthesis_all_orders(L, batch, p->ptS, p->ptE, p->d_ptk_off, p->ws_xS, p->ws_xE,
+                                            p->ws_g, p->d_status, s);
+            p->launches += 1;
+        } else {
+            e = synthesis_all_orders(L, batch, p->pt, p->ws_a, p->ws_g, s);
+        }
     }
     if (e == cudaSuccess) {  // Eq. (18): fold into ring bins, inverse ring DFTs
         Span sp(p, SHT_STAGE_RING_IDFT, s);

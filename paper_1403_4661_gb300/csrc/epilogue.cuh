@@ -1,0 +1,68 @@
+// Epilogues shared by the float64 and the tensor-core contractions: one output row r and the four
+// columns c0..c0+3 of one signal, (+m re, +m im, -m re, -m im).
+#pragma once
+
+#include "sht_internal.cuh"
+
+namespace sht {
+
+struct EpiArgs {
+    double *C; int64_t ldc;
+    const double *C0;   // EPI_SUB
+    int m, L, N;
+    double2 *coeffs;    // EPI_SOLVE
+    double *W;          // EPI_ALIAS
+};
+
+template <int EPI>
+__device__ __forceinline__ void epilogue_row4(const EpiArgs &p, int r, int c0, const double v[4]) {
+    const int m = p.m, N = p.N;
+    if (EPI == EPI_STORE || EPI == EPI_SOLVE) {
+        double *cr = p.C + (int64_t)r * p.ldc + c0;
+        if (c0 + 4 <= N && (p.ldc & 1) == 0) {
+            *reinterpret_cast<double2 *>(cr) = make_double2(v[0], v[1]);
+            *reinterpret_cast<double2 *>(cr + 2) = make_double2(v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (c0 + j < N) cr[j] = v[j];
+        }
+    }
+    if (EPI == EPI_SUB) {
+        const double *c0r = p.C0 + (int64_t)r * p.ldc + c0;
+        double *cr = p.C + (int64_t)r * p.ldc + c0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cr[j] = c0r[j] - v[j];
+    }
+    if (EPI == EPI_SOLVE) {
+        // row r is degree l = m + r; columns (b, +m re/im, -m re/im)
+        const int64_t L2 = (int64_t)p.L * p.L;
+        const int l = m + r, b = c0 >> 2;
+        double2 *cb = p.coeffs + (int64_t)b * L2 + (int64_t)l * l + l;
+        cb[m] = make_double2(v[0], v[1]);
+        if (m > 0) {
+            const double sg = (m & 1) ? -1.0 : 1.0;   // f_l^{-m} = (-1)^m F_l^{-}
+            cb[-m] = make_double2(sg * v[2], sg * v[3]);
+        }
+    }
+    if (EPI == EPI_ALIAS) {
+        // row r is ring k = r < m; subtract G_{+m}, G_{-m} from bins a, -a of ring k
+        const int k = r, b = c0 >> 2;
+        const int a = alias_bin(m, k);
+        const int o = a < 0 ? -a : a;
+        double *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
+        if (a == 0) {
+            w[0] -= v[0] + v[2];
+            w[1] -= v[1] + v[3];
+        } else {
+            const int sp = a > 0 ? 0 : 2;   // slot of bin a  (+o or -o)
+            const int sm = 2 - sp;          // slot of bin -a
+            w[sp] -= v[0];
+            w[sp + 1] -= v[1];
+            w[sm] -= v[2];
+            w[sm + 1] -= v[3];
+        }
+    }
+}
+
+}  // namespace sht

@@ -10,6 +10,7 @@
 //  alias      G_{+-m}(theta_k), k < m, subtracted from bin alias_k(+-m) of ring k (Eqs. (15)-(16))
 #include <algorithm>
 
+#include "epilogue.cuh"
 #include "sht_internal.cuh"
 
 namespace sht {
@@ -42,56 +43,11 @@ __host__ __device__ __forceinline__ int64_t ceil_sum(int64_t x, int64_t bm) {
     return bm * q * (q + 1) / 2 + r * (q + 1);
 }
 
-// One output row r and the four columns c0..c0+3 of one signal: (+m re, +m im, -m re, -m im).
 template <int EPI>
 __device__ __forceinline__ void epilogue(const Params &p, double *C, int64_t ldc, int m, int N,
                                          int r, int c0, const double v[4]) {
-    if (EPI == EPI_STORE || EPI == EPI_SOLVE) {
-        double *cr = C + (int64_t)r * ldc + c0;
-        if (c0 + 4 <= N && (ldc & 1) == 0) {
-            *reinterpret_cast<double2 *>(cr) = make_double2(v[0], v[1]);
-            *reinterpret_cast<double2 *>(cr + 2) = make_double2(v[2], v[3]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (c0 + j < N) cr[j] = v[j];
-        }
-    }
-    if (EPI == EPI_SUB) {
-        const double *c0r = p.C0 + (int64_t)r * ldc + c0;
-        double *cr = C + (int64_t)r * ldc + c0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cr[j] = c0r[j] - v[j];
-    }
-    if (EPI == EPI_SOLVE) {
-        // row r is degree l = m + r; columns (b, +m re/im, -m re/im)
-        const int64_t L2 = (int64_t)p.L * p.L;
-        const int l = m + r, b = c0 >> 2;
-        double2 *cb = p.coeffs + (int64_t)b * L2 + (int64_t)l * l + l;
-        cb[m] = make_double2(v[0], v[1]);
-        if (m > 0) {
-            const double sg = (m & 1) ? -1.0 : 1.0;   // f_l^{-m} = (-1)^m F_l^{-}
-            cb[-m] = make_double2(sg * v[2], sg * v[3]);
-        }
-    }
-    if (EPI == EPI_ALIAS) {
-        // row r is ring k = r < m; subtract G_{+m}, G_{-m} from bins a, -a of ring k
-        const int k = r, b = c0 >> 2;
-        const int a = alias_bin(m, k);
-        const int o = a < 0 ? -a : a;
-        double *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
-        if (a == 0) {
-            w[0] -= v[0] + v[2];
-            w[1] -= v[1] + v[3];
-        } else {
-            const int sp = a > 0 ? 0 : 2;   // slot of bin a  (+o or -o)
-            const int sm = 2 - sp;          // slot of bin -a
-            w[sp] -= v[0];
-            w[sp + 1] -= v[1];
-            w[sm] -= v[2];
-            w[sm + 1] -= v[3];
-        }
-    }
+    EpiArgs e{C, ldc, p.C0, m, p.L, N, p.coeffs, p.W};
+    epilogue_row4<EPI>(e, r, c0, v);
 }
 
 // Tile BM x BN, each thread TM rows x 4 columns (one signal), K in steps of BK through shared

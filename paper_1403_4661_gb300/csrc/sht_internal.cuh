@@ -20,6 +20,7 @@
 // ring DFTs carry 1/N_k, so that bin j of ring k equals sum_{m = j mod N_k} G_m(theta_k).
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,6 +90,15 @@ struct sht_plan_s {
     double plan_seconds = 0.0;
     double order_seconds = 0.0;
     int64_t launches = 0;
+    // SHT_F64_TENSOR: slices of the tables, their exponents and per-order offsets
+    __nv_bfloat16 *ptS = nullptr, *piS = nullptr;
+    int *ptE = nullptr, *piE = nullptr;
+    int64_t *d_ptk_off = nullptr, *d_pik_off = nullptr;
+    std::vector<int64_t> ptk_off, pik_off;
+    int *d_status = nullptr;
+    // per-call slices (workspace)
+    __nv_bfloat16 *ws_xS = nullptr, *ws_wS = nullptr;
+    int *ws_xE = nullptr, *ws_wE = nullptr;
     // stage timing (sht_plan_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -162,6 +172,46 @@ cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coe
 // adjoint chain: U[k] (k < m) = the bins of ring k that orders +m / -m alias to
 cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U,
                               cudaStream_t s);
+
+// tc_gemm.cu: float64-accurate contractions on the tensor cores from exact BF16 slices
+constexpr int kTcSlices = 8;     // slices per operand
+constexpr int kTcSliceBits = 7;  // bits per slice
+struct TcOperand {               // K-major slices of a real matrix: [slice][rows][kp] BF16
+    const __nv_bfloat16 *data;
+    const int *expo;             // per-row power-of-two scale
+    int64_t slice_stride;        // rows * kp
+    int kp;                      // padded K (multiple of 8)
+};
+struct TcEpilogue {
+    double *C; int64_t ldc;
+    const double *C0;
+    int m, L;
+    double2 *coeffs;
+    double *W;
+};
+cudaError_t tc_prepare_kernels();
+cudaError_t tc_slice_rows(const double *X, int64_t ld, int rows, int K, int kp, __nv_bfloat16 *out,
+                          int64_t sstride, int *expo, cudaStream_t s);
+cudaError_t tc_slice_cols(const double *X, int64_t ld, int K, int cols, int kp, __nv_bfloat16 *out,
+                          int64_t sstride, int *expo, cudaStream_t s);
+constexpr int kNumSMs = 152;
+// Plan tables: slices of every order's P~ block (inverses = false; slice block m at
+// kTcSlices * L * koff[m] elements, exponents at m * L) or P_m^{-1} block (inverses = true; slices
+// at kTcSlices * koff[m], exponents at rows_off(L, m)).
+cudaError_t tc_slice_table(const double *tab, int L, bool inverses, const int64_t *koff,
+                           __nv_bfloat16 *out, int *expo, cudaStream_t s);
+// Order-major coefficients X of a batch: slices of block m at kTcSlices * 4B * koff[m], exponents
+// at m * 4B.
+cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t *koff,
+                            __nv_bfloat16 *out, int *expo, cudaStream_t s);
+// C = A B^T (A: M x K slices, B: N x K slices) with an epilogue; split-K over `part` when the
+// output tiles alone cannot fill the SMs.
+cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K, int epi,
+                    const TcEpilogue &ep, int *status, cudaStream_t s, double *part = nullptr,
+                    int64_t part_cap = 0, int64_t *launches = nullptr);
+cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *ptS, const int *ptE,
+                                    const int64_t *kpoff, const __nv_bfloat16 *xS, const int *xE,
+                                    double *Gt, int *status, cudaStream_t s);
 
 // planner.cu: greedy condition-number ordering (indices into the equiangular set)
 sht_status greedy_order(int L, std::vector<int> &order);

@@ -22,13 +22,15 @@ SHT_OK = 0
 SHT_STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3: "SHT_ERR_OOM",
               4: "SHT_ERR_CUDA", 5: "SHT_ERR_NOT_CONVERGED", 6: "SHT_ERR_TIMEOUT"}
 SHT_F64 = 0
+SHT_F64_TENSOR = 1
+DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR}
 SHT_ORDER_GREEDY = 0
 SHT_ORDER_SIMPLE = 1
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
             "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
-            "sht_forward_noalloc"]
+            "sht_forward_noalloc", "sht_plan_check"]
 STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
 
 
@@ -73,6 +75,7 @@ def load_library(path=LIB_PATH):
     lib.sht_get_info.argtypes = [P, ctypes.POINTER(ShtInfo)]
     lib.sht_status_string.argtypes = [ctypes.c_int]
     lib.sht_status_string.restype = ctypes.c_char_p
+    lib.sht_plan_check.argtypes = [P]
     lib.sht_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.sht_plan_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.sht_last_error_message.argtypes = []
@@ -136,6 +139,10 @@ def sht_get_info(h):
     info = ShtInfo()
     _check(load_library().sht_get_info(h, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in ShtInfo._fields_}
+
+
+def sht_plan_check(h):
+    _check(load_library().sht_plan_check(h))
 
 
 def sht_plan_set_timing(h, enable):
@@ -216,6 +223,8 @@ class Plan:
 
     def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64):
         self.L = int(L)
+        dtype = DTYPES.get(dtype, dtype)
+        self.dtype = dtype
         if theta is not None:
             self.handle = sht_plan_with_thetas(self.L, theta, dtype)
         else:
@@ -239,6 +248,10 @@ class Plan:
 
     def info(self):
         return sht_get_info(self.handle)
+
+    def check(self):
+        """Synchronise and raise if a bounded device wait gave up since the last check."""
+        sht_plan_check(self.handle)
 
     def set_timing(self, enable=True):
         sht_plan_set_timing(self.handle, enable)
