@@ -111,6 +111,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+// v * 2^e as a float64, assembled with integer operations only (round to nearest, ties away from
+// zero); the float64 pipe is 1/64 of the integer rate.  Results below the normal range are 0.
+__device__ __forceinline__ double i64_scaled(long long v, int e) {
+    if (v == 0) return 0.0;
+    const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+    unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+    int msb = 63 - __clzll(a);
+    unsigned long long m;
+    if (msb > 52) {
+        const int sh = msb - 52;
+        m = (a + (1ull << (sh - 1))) >> sh;
+        if (m >> 53) { m >>= 1; ++msb; }
+    } else {
+        m = a << (52 - msb);
+    }
+    const int biased = msb + e + 1023;
+    if (biased <= 0) return 0.0;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)biased << 52) |
+                                            (m & 0xFFFFFFFFFFFFFull)));
+}
+
 // Shared-memory matrix descriptor: no swizzle, K-major; lbo = byte step between core matrices
 // along K, sbo = byte step between 8-row groups along M (or N).
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -441,7 +462,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
         double v[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            v[q] = (c0 + q < N) ? scalbn((double)acc[4 * g + q], er + eB[c0 + q] - ACC_SHIFT) : 0.0;
+            v[q] = (c0 + q < N) ? i64_scaled(acc[4 * g + q], er + eB[c0 + q] - ACC_SHIFT) : 0.0;
         if (SPLIT) {
             double *pp = p.part + ((int64_t)blockIdx.y * M + row) * N + c0;
 #pragma unroll
