@@ -173,7 +173,9 @@ def run_reference(args):
 
 def _config(args):
     arith = {"f64": "plain float64",
-             "f64_tensor": "float64-accurate, contractions on the BF16 tensor cores from exact slices"}
+             "f64_tensor": "float64-accurate, contractions on the BF16 tensor cores from exact slices",
+             "bf16_refined": "forward by iterative refinement with BF16 contractions, float64-accurate residual",
+             "bf16x2_refined": "forward by iterative refinement with BF16x2 contractions, float64-accurate residual"}
     return {"workload": f"{args.batch} complex signals at L={args.L}, f_lm re/im iid N(0,1)/(l+1); "
                         f"inverse SHT then forward SHT, {arith.get(getattr(args, 'dtype', 'f64'))}",
             "arithmetic": getattr(args, "dtype", "f64"),
@@ -209,6 +211,11 @@ def run_ours(args):
     t0 = time.time()
     plan = Plan(L, dtype=args.dtype)  # greedy ring ordering on the GPU, tables, per-order inverses
     plan_s = time.time() - t0
+    if args.dtype.endswith("refined"):
+        if args.refine_iters > 0:
+            plan.set_refinement(args.refine_iters, 0.0)   # fixed count: capturable
+        elif not args.no_graph:
+            args.no_graph = True  # tolerance-driven refinement synchronises each iteration
     plan.reserve(B)
     c_host = torch.from_numpy(synth.decaying_coeffs(L, B, 1000 + rank)).pin_memory()
     c = c_host.to(dev)
@@ -316,7 +323,7 @@ def run_ours(args):
     sec = syn_ms / syn_n * 1e-3
     sm_mhz = (clk or {}).get("sm_mhz") or FP64_NOMINAL_MHZ
     peaks = _peaks()
-    if args.dtype == "f64_tensor":
+    if args.dtype != "f64":
         # 36 BF16 slice-pair products per float64 product (8 slices a side, s + t <= 9)
         achieved = 36.0 * flops / sec / 1e12
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
@@ -342,7 +349,9 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.dtype == "f64" else "f64 (bf16 tensor-core slices)",
+        "vs_baseline": None,
+        "dtype": {"f64": "f64", "f64_tensor": "f64 (bf16 tensor-core slices)"}.get(
+            args.dtype, "bf16 contractions + f64 residual (refined)"),
         "data": "synthetic",
         "config": dict(_config(args), parallelism=f"dp{ws}" if ws > 1 else "single GPU"),
         "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e},
@@ -366,7 +375,10 @@ def main():
     ap.add_argument("--L", type=int, default=1024)
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--dtype", default="f64_tensor", choices=["f64", "f64_tensor"])
+    ap.add_argument("--dtype", default="f64_tensor",
+                    choices=["f64", "f64_tensor", "bf16_refined", "bf16x2_refined"])
+    ap.add_argument("--refine-iters", type=int, default=0,
+                    help="refined forms: fixed iteration count (0: iterate to 1e-12)")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of one CUDA graph per step")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -58,10 +58,19 @@ typedef enum {
  *                   Legendre recursion stay in float64.  Errors are of the order of a float64
  *                   contraction.  The plan additionally holds the slices of its tables (about
  *                   2x the float64 tables).  The adjoints run the float64 kernels.
+ *   SHT_BF16_REFINED, SHT_BF16X2_REFINED
+ *                   forward by iterative refinement: x_0 = F_lo(s), x_{i+1} = x_i + F_lo(s - A x_i),
+ *                   F_lo being the forward with its contractions on the tensor cores from 1 (BF16)
+ *                   or 2 (BF16 x 2, ~15-bit) slices per operand with FP32 accumulation, and A the
+ *                   float64-accurate inverse of SHT_F64_TENSOR; the ring DFTs, the Legendre
+ *                   recursion and the residual s - A x stay float64-accurate.  The inverse and the
+ *                   adjoints are those of SHT_F64_TENSOR.  See sht_plan_set_refinement.
  */
 typedef enum {
     SHT_F64 = 0,
-    SHT_F64_TENSOR = 1
+    SHT_F64_TENSOR = 1,
+    SHT_BF16_REFINED = 2,
+    SHT_BF16X2_REFINED = 3
 } sht_dtype;
 
 /* Plan flags: ring ordering (Sec. III-E). */
@@ -167,6 +176,17 @@ sht_status sht_forward_noalloc(sht_plan_t plan, const void *d_samples, void *d_c
                                int64_t batch, void *stream);
 
 /*
+ * sht_plan_set_refinement - iteration control of the refined forward (SHT_BF16*_REFINED plans).
+ *   tol > 0: iterate until the largest |Re|, |Im| over the last update of the coefficients is
+ *   <= tol, at most max_iters iterations; each iteration reads that maximum to the host
+ *   (synchronises the call's stream); not reaching tol returns SHT_ERR_NOT_CONVERGED with the last
+ *   iterate in the output.  tol == 0: exactly max_iters iterations and no synchronisation (the
+ *   call can be captured in a CUDA graph).  Defaults: max_iters = 10, tol = 1e-11.
+ *   sht_get_info reports the iterations and the last update of the most recent refined call.
+ */
+sht_status sht_plan_set_refinement(sht_plan_t plan, int max_iters, double tol);
+
+/*
  * sht_plan_check - wait for the plan's queued work (synchronises the device) and report whether a
  *   bounded wait inside a tensor-core kernel gave up since the last check (SHT_ERR_TIMEOUT; the
  *   results of the affected call are then invalid).  Clears the flag.
@@ -183,6 +203,8 @@ typedef struct {
     double plan_seconds;       /* wall time of plan creation */
     double order_seconds;      /* part of it spent ordering the rings */
     int64_t kernel_launches;   /* kernels this plan's transform calls have launched so far */
+    int refine_iterations;     /* refined forward: iterations of the most recent call */
+    double refine_last_update; /* refined forward: largest |Re|, |Im| of its last update (tol > 0) */
 } sht_info;
 
 /* Stages of the transforms, for sht_plan_stage_times. */

@@ -38,6 +38,8 @@ void free_workspaces(sht_plan_t p) {
     cudaFree(p->ws_xS); cudaFree(p->ws_wS); cudaFree(p->ws_xE); cudaFree(p->ws_wE);
     p->ws_xS = p->ws_wS = nullptr;
     p->ws_xE = p->ws_wE = nullptr;
+    cudaFree(p->ws_r); cudaFree(p->ws_dx);
+    p->ws_r = p->ws_dx = nullptr;
     p->ws_batch = 0;
     p->ws_bytes = 0;
 }
@@ -49,7 +51,7 @@ void destroy(sht_plan_t p) {
     if (dev != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_theta); cudaFree(p->pt); cudaFree(p->pinv);
     cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
-    cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status);
+    cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
     dft_plan_destroy(p->dft);
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -76,7 +78,17 @@ sht_status ensure_workspace(sht_plan_t p, int64_t batch) {
     }
     p->ws_batch = batch;
     p->ws_bytes = 2 * a + g + sp;
-    if (p->dtype == SHT_F64_TENSOR) {
+    if (p->refine_nsl > 0) {
+        const size_t io = sizeof(double2) * (size_t)p->L * p->L * (size_t)batch;
+        e = cudaMalloc(&p->ws_r, io);
+        if (e == cudaSuccess) e = cudaMalloc(&p->ws_dx, io);
+        if (e != cudaSuccess) {
+            free_workspaces(p);
+            return cuda_check(e, "workspace allocation");
+        }
+        p->ws_bytes += 2 * io;
+    }
+    if (p->dtype != SHT_F64) {
         const size_t Nc = 4 * (size_t)batch;
         const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
         const size_t ws = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)((p->L + 7) & ~7);
@@ -167,9 +179,12 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
     if (st == SHT_OK) {
         e = cudaMalloc(&p->d_status, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&p->d_refine_max, sizeof(double));
         if (e != cudaSuccess) st = cuda_check(e, "status word");
     }
-    if (st == SHT_OK && dtype == SHT_F64_TENSOR) st = build_tensor_tables(p, s, tc_bytes);
+    if (dtype == SHT_BF16_REFINED) p->refine_nsl = 1;
+    if (dtype == SHT_BF16X2_REFINED) p->refine_nsl = 2;
+    if (st == SHT_OK && dtype != SHT_F64) st = build_tensor_tables(p, s, tc_bytes);
     cudaStreamDestroy(s);
     if (st != SHT_OK) { destroy(p); *out = nullptr; return st; }
     p->table_bytes = pt_bytes + pi_bytes + dft_bytes + tc_bytes + sizeof(double) * L;
@@ -238,6 +253,132 @@ sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch
     return SHT_OK;
 }
 
+// Forward transform (Procedure 1 in bin space).  Float64 plans run the float64 kernels; the other
+// plans run the contractions on the tensor cores with `nsl` slices per operand (kTcSlices:
+// float64-accurate; fewer: the low-precision forward of the refinement).
+cudaError_t forward_impl(sht_plan_t p, const double2 *d_samples, double2 *d_coeffs, int64_t batch,
+                         cudaStream_t s, int nsl) {
+    const int L = p->L;
+    const int64_t Nc = 4 * batch;
+    double *W = p->ws_a, *F = p->ws_b;
+    cudaError_t e;
+    {
+        Span sp(p, SHT_STAGE_RING_DFT, s);
+        e = ring_dft_to_bins(L, p->dft, d_samples, W, batch, true, s);
+    }
+    p->launches += ring_launches(L);
+    if (p->dtype != SHT_F64) {
+        const int64_t cap = (int64_t)kSplitCap * L * Nc;
+        for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
+            const int n = L - m, kp = (n + 7) & ~7;
+            const TcOperand bins{p->ws_wS, p->ws_wE, Nc * kp, kp};
+            {   // Eq. (14) on the tensor cores: slices of g_m, then F_m = P_m^{-1} g_m
+                Span sp(p, SHT_STAGE_SOLVE, s);
+                e = tc_slice_cols(W + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
+                const TcOperand inv{p->piS + (int64_t)kTcSlices * p->pik_off[m], p->piE + rows_off(L, m),
+                                    (int64_t)n * kp, kp};
+                const TcEpilogue ep{F + rows_off(L, m) * Nc, Nc, nullptr, m, L, d_coeffs, nullptr};
+                if (e == cudaSuccess)
+                    e = tc_gemm(inv, bins, n, (int)Nc, n, EPI_SOLVE, ep, p->d_status, s, p->ws_part, cap,
+                                &p->launches, nsl);
+                p->launches += 1;
+            }
+            if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): rings k < m
+                Span sp(p, SHT_STAGE_ALIAS, s);
+                e = tc_slice_cols(F + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
+                const TcOperand low{p->ptS + (int64_t)kTcSlices * L * p->ptk_off[m], p->ptE + (int64_t)m * L,
+                                    (int64_t)L * kp, kp};
+                const TcEpilogue ep{nullptr, Nc, nullptr, m, L, nullptr, W};
+                if (e == cudaSuccess)
+                    e = tc_gemm(low, bins, m, (int)Nc, n, EPI_ALIAS, ep, p->d_status, s, p->ws_part, cap,
+                                &p->launches, nsl);
+                p->launches += 1;
+            }
+        }
+        return e;
+    }
+    GemmArgs ga{};
+    ga.L = L; ga.batch = batch; ga.coeffs = d_coeffs; ga.W = W;
+    ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.launches = &p->launches;
+    for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
+        const int n = L - m;
+        ga.m = m;
+        {   // Eq. (14): F_m = P_m^{-1} g_m, with g_m = bins +-m of rings k >= m (alias-free by now)
+            Span sp(p, SHT_STAGE_SOLVE, s);
+            e = gemm_f64(false, n, n, (int)Nc, p->pinv + pinv_off(L, m), n, W + rows_off(L, m) * Nc,
+                         Nc, F + rows_off(L, m) * Nc, Nc, EPI_SOLVE, ga, s);
+        }
+        if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): remove orders +-m from rings k < m
+            Span sp(p, SHT_STAGE_ALIAS, s);
+            e = gemm_f64(false, m, n, (int)Nc, p->pt + pt_off(L, m), n, F + rows_off(L, m) * Nc, Nc,
+                         nullptr, Nc, EPI_ALIAS, ga, s);
+        }
+    }
+    return e;
+}
+
+// Inverse transform (Procedure 2), float64-accurate for every plan arithmetic.
+cudaError_t inverse_impl(sht_plan_t p, const double2 *d_coeffs, double2 *d_samples, int64_t batch,
+                         cudaStream_t s) {
+    const int L = p->L;
+    cudaError_t e;
+    {
+        Span sp(p, SHT_STAGE_LAYOUT, s);
+        e = coeffs_to_orders(L, batch, d_coeffs, p->ws_a, s);
+    }
+    if (e == cudaSuccess) {  // Eq. (11): G_{+-m}(theta_k) for every order and ring
+        Span sp(p, SHT_STAGE_SYNTHESIS, s);
+        if (p->dtype != SHT_F64) {
+            e = tc_slice_orders(p->ws_a, L, batch, p->d_ptk_off, p->ws_xS, p->ws_xE, s);
+            if (e == cudaSuccess)
+                e = tc_synthesis_all_orders(L, batch, p->ptS, p->ptE, p->d_ptk_off, p->ws_xS, p->ws_xE,
+                                            p->ws_g, p->d_status, s);
+            p->launches += 1;
+        } else {
+            e = synthesis_all_orders(L, batch, p->pt, p->ws_a, p->ws_g, s);
+        }
+    }
+    if (e == cudaSuccess) {  // Eq. (18): fold into ring bins, inverse ring DFTs
+        Span sp(p, SHT_STAGE_RING_IDFT, s);
+        e = fold_ring_idft(L, p->dft, p->ws_g, d_samples, batch, s);
+    }
+    p->launches += 2 + ring_launches(L);
+    return e;
+}
+
+// Iterative refinement of the forward transform: x_0 = F_lo(s), then
+// x_{i+1} = x_i + F_lo(s - A x_i), A the float64-accurate inverse, F_lo the forward with
+// low-precision (refine_nsl slices) contractions.  With a tolerance, each iteration reads
+// max |Re, Im (x_{i+1} - x_i)| to the host and stops below it; with tolerance 0 it runs exactly
+// refine_max_iters iterations and never synchronises (capturable in a CUDA graph).
+sht_status refined_forward(sht_plan_t p, const double2 *d_samples, double2 *d_coeffs, int64_t batch,
+                           cudaStream_t s) {
+    const int64_t n = (int64_t)p->L * p->L * batch;
+    cudaError_t e = forward_impl(p, d_samples, d_coeffs, batch, s, p->refine_nsl);
+    int it = 0;
+    double last = INFINITY;
+    bool converged = false;
+    for (; it < p->refine_max_iters && e == cudaSuccess; ++it) {
+        e = inverse_impl(p, d_coeffs, p->ws_r, batch, s);
+        if (e == cudaSuccess) e = residual(n, d_samples, p->ws_r, s);
+        if (e == cudaSuccess) e = forward_impl(p, p->ws_r, p->ws_dx, batch, s, p->refine_nsl);
+        if (e == cudaSuccess) e = update_with_max(n, d_coeffs, p->ws_dx, p->d_refine_max, s);
+        p->launches += 2;
+        if (e == cudaSuccess && p->refine_tol > 0.0) {
+            e = cudaMemcpyAsync(&last, p->d_refine_max, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess && last <= p->refine_tol) { ++it; converged = true; break; }
+        }
+    }
+    p->refine_iters = it;
+    p->refine_last = last;
+    if (e != cudaSuccess) return cuda_check(e, "sht_forward (refinement)");
+    if (p->refine_tol > 0.0 && !converged)
+        return set_error(SHT_ERR_NOT_CONVERGED, "refinement did not reach the tolerance in max_iters iterations");
+    return SHT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -263,7 +404,7 @@ sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if (dtype != SHT_F64 && dtype != SHT_F64_TENSOR) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if ((int)dtype < 0 || (int)dtype > SHT_BF16X2_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     if (!theta_host) return set_error(SHT_ERR_INVALID_ARG, "theta_host is NULL");
     std::vector<double> th(theta_host, theta_host + L);
     // the equiangular set's end point pi (2L-1)/(2L-1) may round one ulp past pi: allow 1e-12
@@ -276,7 +417,7 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if (dtype != SHT_F64 && dtype != SHT_F64_TENSOR) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if ((int)dtype < 0 || (int)dtype > SHT_BF16X2_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     std::vector<int> order(L);
     auto t0 = std::chrono::steady_clock::now();
     if ((flags & SHT_ORDER_MASK) == SHT_ORDER_SIMPLE) {
@@ -326,6 +467,16 @@ sht_status sht_get_info(sht_plan_t p, sht_info *out) {
     out->plan_seconds = p->plan_seconds;
     out->order_seconds = p->order_seconds;
     out->kernel_launches = p->launches;
+    out->refine_iterations = p->refine_iters;
+    out->refine_last_update = p->refine_last;
+    return SHT_OK;
+}
+
+sht_status sht_plan_set_refinement(sht_plan_t p, int max_iters, double tol) {
+    if (!p) return set_error(SHT_ERR_INVALID_ARG, "plan is NULL");
+    if (max_iters < 0 || !(tol >= 0.0)) return set_error(SHT_ERR_INVALID_ARG, "max_iters < 0 or tol < 0");
+    p->refine_max_iters = max_iters;
+    p->refine_tol = tol;
     return SHT_OK;
 }
 
@@ -373,65 +524,9 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int L = p->L;
-    const int64_t Nc = 4 * batch;
-    double *W = p->ws_a, *F = p->ws_b;
-    cudaError_t e;
-    {
-        Span sp(p, SHT_STAGE_RING_DFT, s);
-        e = ring_dft_to_bins(L, p->dft, (const double2 *)d_samples, W, batch, true, s);
-    }
-    if (p->dtype == SHT_F64_TENSOR) {
-        const int64_t cap = (int64_t)kSplitCap * L * Nc;
-        for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
-            const int n = L - m, kp = (n + 7) & ~7;
-            const TcOperand bins{p->ws_wS, p->ws_wE, Nc * kp, kp};
-            {   // Eq. (14) on the tensor cores: slices of g_m, then F_m = P_m^{-1} g_m
-                Span sp(p, SHT_STAGE_SOLVE, s);
-                e = tc_slice_cols(W + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
-                const TcOperand inv{p->piS + (int64_t)kTcSlices * p->pik_off[m], p->piE + rows_off(L, m),
-                                    (int64_t)n * kp, kp};
-                const TcEpilogue ep{F + rows_off(L, m) * Nc, Nc, nullptr, m, L, (double2 *)d_coeffs, nullptr};
-                if (e == cudaSuccess)
-                    e = tc_gemm(inv, bins, n, (int)Nc, n, EPI_SOLVE, ep, p->d_status, s, p->ws_part, cap,
-                                &p->launches);
-                p->launches += 1;
-            }
-            if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): rings k < m
-                Span sp(p, SHT_STAGE_ALIAS, s);
-                e = tc_slice_cols(F + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
-                const TcOperand low{p->ptS + (int64_t)kTcSlices * L * p->ptk_off[m], p->ptE + (int64_t)m * L,
-                                    (int64_t)L * kp, kp};
-                const TcEpilogue ep{nullptr, Nc, nullptr, m, L, nullptr, W};
-                if (e == cudaSuccess)
-                    e = tc_gemm(low, bins, m, (int)Nc, n, EPI_ALIAS, ep, p->d_status, s, p->ws_part, cap,
-                                &p->launches);
-                p->launches += 1;
-            }
-        }
-        p->launches += ring_launches(L);
-        return cuda_check(e, "sht_forward");
-    }
-    GemmArgs ga{};
-    ga.L = L; ga.batch = batch; ga.coeffs = (double2 *)d_coeffs; ga.W = W;
-    ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
-    ga.launches = &p->launches;
-    for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
-        const int n = L - m;
-        ga.m = m;
-        {   // Eq. (14): F_m = P_m^{-1} g_m, with g_m = bins +-m of rings k >= m (alias-free by now)
-            Span sp(p, SHT_STAGE_SOLVE, s);
-            e = gemm_f64(false, n, n, (int)Nc, p->pinv + pinv_off(L, m), n, W + rows_off(L, m) * Nc,
-                         Nc, F + rows_off(L, m) * Nc, Nc, EPI_SOLVE, ga, s);
-        }
-        if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): remove orders +-m from rings k < m
-            Span sp(p, SHT_STAGE_ALIAS, s);
-            e = gemm_f64(false, m, n, (int)Nc, p->pt + pt_off(L, m), n, F + rows_off(L, m) * Nc, Nc,
-                         nullptr, Nc, EPI_ALIAS, ga, s);
-        }
-    }
-    p->launches += ring_launches(L);
-    return cuda_check(e, "sht_forward");
+    if (p->refine_nsl > 0) return refined_forward(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s);
+    return cuda_check(forward_impl(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s, kTcSlices),
+                      "sht_forward");
 }
 
 sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int64_t batch,
@@ -439,31 +534,9 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     sht_status st = check_io(p, d_coeffs, d_samples, batch);
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
-    cudaStream_t s = (cudaStream_t)stream;
-    const int L = p->L;
-    cudaError_t e;
-    {
-        Span sp(p, SHT_STAGE_LAYOUT, s);
-        e = coeffs_to_orders(L, batch, (const double2 *)d_coeffs, p->ws_a, s);
-    }
-    if (e == cudaSuccess) {  // Eq. (11): G_{+-m}(theta_k) for every order and ring
-        Span sp(p, SHT_STAGE_SYNTHESIS, s);
-        if (p->dtype == SHT_F64_TENSOR) {
-            e = tc_slice_orders(p->ws_a, L, batch, p->d_ptk_off, p->ws_xS, p->ws_xE, s);
-            if (e == cudaSuccess)
-                e = tc_synthesis_all_orders(L, batch, p->ptS, p->ptE, p->d_ptk_off, p->ws_xS, p->ws_xE,
-                                            p->ws_g, p->d_status, s);
-            p->launches += 1;
-        } else {
-            e = synthesis_all_orders(L, batch, p->pt, p->ws_a, p->ws_g, s);
-        }
-    }
-    if (e == cudaSuccess) {  // Eq. (18): fold into ring bins, inverse ring DFTs
-        Span sp(p, SHT_STAGE_RING_IDFT, s);
-        e = fold_ring_idft(L, p->dft, p->ws_g, (double2 *)d_samples, batch, s);
-    }
-    p->launches += 2 + ring_launches(L);
-    return cuda_check(e, "sht_inverse");
+    return cuda_check(inverse_impl(p, (const double2 *)d_coeffs, (double2 *)d_samples, batch,
+                                   (cudaStream_t)stream),
+                      "sht_inverse");
 }
 
 sht_status sht_inverse_adjoint(sht_plan_t p, const void *d_samples, void *d_coeffs, int64_t batch,

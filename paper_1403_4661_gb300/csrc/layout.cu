@@ -70,7 +70,52 @@ __global__ void k_gather_alias_bins(int L, int m, int64_t batch, const double *_
     u[2] = w[sn]; u[3] = w[sn + 1];
 }
 
+__global__ void k_residual(int64_t n, const double2 *__restrict__ s_in, double2 *__restrict__ r) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double2 a = s_in[t], b = r[t];
+    r[t] = make_double2(a.x - b.x, a.y - b.y);
+}
+
+// x += dx; the largest |Re dx|, |Im dx| goes to *mx through an integer atomicMax on the bit
+// pattern (non-negative doubles order like their bits).
+__global__ void k_update_max(int64_t n, double2 *__restrict__ x, const double2 *__restrict__ dx,
+                             unsigned long long *__restrict__ mx) {
+    __shared__ unsigned long long red[8];
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long m = 0;
+    if (t < n) {
+        const double2 a = x[t], d = dx[t];
+        x[t] = make_double2(a.x + d.x, a.y + d.y);
+        const unsigned long long ur = (unsigned long long)__double_as_longlong(d.x) & 0x7FFFFFFFFFFFFFFFull;
+        const unsigned long long ui = (unsigned long long)__double_as_longlong(d.y) & 0x7FFFFFFFFFFFFFFFull;
+        m = ur > ui ? ur : ui;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long q = __shfl_xor_sync(0xffffffffu, m, o);
+        m = q > m ? q : m;
+    }
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+        atomicMax(mx, m);
+    }
+}
+
 }  // namespace
+
+cudaError_t residual(int64_t n, const double2 *s_in, double2 *r, cudaStream_t s) {
+    k_residual<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, s_in, r);
+    return cudaGetLastError();
+}
+
+cudaError_t update_with_max(int64_t n, double2 *x, const double2 *dx, double *mx, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(double), s);
+    if (e != cudaSuccess) return e;
+    k_update_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, x, dx, (unsigned long long *)mx);
+    return cudaGetLastError();
+}
 
 cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U, cudaStream_t s) {
     int64_t n = (int64_t)m * batch;

@@ -99,6 +99,14 @@ struct sht_plan_s {
     // per-call slices (workspace)
     __nv_bfloat16 *ws_xS = nullptr, *ws_wS = nullptr;
     int *ws_xE = nullptr, *ws_wE = nullptr;
+    // refinement (SHT_BF16_REFINED, SHT_BF16X2_REFINED)
+    int refine_nsl = 0;           // slices of the low-precision forward; 0: no refinement
+    int refine_max_iters = 10;
+    double refine_tol = 1e-11;
+    int refine_iters = 0;
+    double refine_last = 0.0;
+    double *d_refine_max = nullptr;
+    double2 *ws_r = nullptr, *ws_dx = nullptr;
     // stage timing (sht_plan_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -169,6 +177,9 @@ cudaError_t coeffs_to_orders(int L, int64_t batch, const double2 *coeffs, double
                              cudaStream_t s);
 cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coeffs,
                              cudaStream_t s);
+// refinement: r = s - r (n complex values); x += dx and max |Re, Im dx| into *mx
+cudaError_t residual(int64_t n, const double2 *s_in, double2 *r, cudaStream_t s);
+cudaError_t update_with_max(int64_t n, double2 *x, const double2 *dx, double *mx, cudaStream_t s);
 // adjoint chain: U[k] (k < m) = the bins of ring k that orders +m / -m alias to
 cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U,
                               cudaStream_t s);
@@ -208,7 +219,7 @@ cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t
 // output tiles alone cannot fill the SMs.
 cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K, int epi,
                     const TcEpilogue &ep, int *status, cudaStream_t s, double *part = nullptr,
-                    int64_t part_cap = 0, int64_t *launches = nullptr);
+                    int64_t part_cap = 0, int64_t *launches = nullptr, int nsl = kTcSlices);
 cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *ptS, const int *ptE,
                                     const int64_t *kpoff, const __nv_bfloat16 *xS, const int *xE,
                                     double *Gt, int *status, cudaStream_t s);

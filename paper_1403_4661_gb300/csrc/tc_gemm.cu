@@ -302,8 +302,15 @@ struct TcArgs {
     double *part;
 };
 
-template <int EPI, bool GROUPED, bool SPLIT>
+// NSL = slices used per operand: kTcSlices for float64-accurate products (exact diagonals,
+// chunked int64 folding), or 1..2 for the low-precision products of the refinement (every pair in
+// one FP32 region over the whole K, converted once at the end).
+template <int EPI, bool GROUPED, bool SPLIT, int NSL>
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
+    constexpr bool EXACT = NSL == S;
+    constexpr int NREG = EXACT ? REGIONS : 1;
+    constexpr uint32_t NCOLS = EXACT ? TMEM_COLS : 64u;
+    constexpr int SHIFT = EXACT ? ACC_SHIFT : 40;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
@@ -336,7 +343,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
         kend = min(K, kbeg + p.kchunk);
     }
 
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), TMEM_COLS);
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), NCOLS);
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
@@ -351,14 +358,14 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
     auto load = [&](int kb, int st) {
         const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
         const int kbase = kb * KB;
-        for (int idx = tid; idx < S * MT * 4; idx += 128) {
+        for (int idx = tid; idx < NSL * MT * 4; idx += 128) {
             const int j = idx & 3, r = (idx >> 2) & (MT - 1), s = idx >> 9;
             const int row = row0 + r, kc = kbase + 8 * j;
             const bool ok = row < M && kc < akp;
             const __nv_bfloat16 *src = ok ? A + s * as + (int64_t)row * akp + kc : A;
             cp_async16(sa + s * (MT * KB * 2) + j * (MT * 16) + (r >> 3) * 128 + (r & 7) * 16, src, ok ? 16 : 0);
         }
-        for (int idx = tid; idx < S * NT * 4; idx += 128) {
+        for (int idx = tid; idx < NSL * NT * 4; idx += 128) {
             const int j = idx & 3, r = (idx >> 2) & (NT - 1), s = idx >> 8;
             const int row = col0 + r, kc = kbase + 8 * j;
             const bool ok = row < N && kc < bkp;
@@ -398,11 +405,11 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
             for (int h = 0; h < 2; ++h) {
                 const int kg = kb * KB + 16 * h;
                 if (kg >= kend) break;
-                if (kg % CHUNK == 0)
+                if (EXACT ? (kg % CHUNK == 0) : (kg == kbeg))
                     for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
-                for (int s = 1; s <= S; ++s)
-                    for (int t = 1; s + t <= S + 1; ++t) {
-                        const int d = s + t, reg = d <= 6 ? d - 2 : 5;
+                for (int s = 1; s <= NSL; ++s)
+                    for (int t = 1; s + t <= NSL + 1; ++t) {
+                        const int d = s + t, reg = EXACT ? (d <= 6 ? d - 2 : 5) : 0;
                         const uint64_t ad = sdesc(sa + (s - 1) * (MT * KB * 2) + 2 * h * (MT * 16), MT * 16, 128);
                         const uint64_t bd = sdesc(sb + (t - 1) * (NT * KB * 2) + 2 * h * (NT * 16), NT * 16, 128);
                         mma_bf16(tbase + reg * NT, ad, bd, kIdesc, fresh[reg] ? 0u : 1u);
@@ -413,27 +420,38 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
         }
         uses[st] += 1;
         const int kdone = (kb + 1) * KB;
-        if (kdone % CHUNK == 0 || kb == nkb - 1) {
+        if ((EXACT && kdone % CHUNK == 0) || kb == nkb - 1) {
             // the commit of this stage covers every MMA issued so far
             const bool w = mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u);
             if (!__syncthreads_and(w)) { ok = false; break; }
             tc_fence_after();
             const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
+            if (EXACT) {
 #pragma unroll
-            for (int reg = 0; reg < REGIONS; ++reg) {
-                // region reg holds diagonal d = reg + 2 (multiples of 2^-7d, exact), or the
-                // rounded sum of d >= 7 for the last region
-                const int d = reg + 2;
-                const float up = reg < REGIONS - 1 ? __int_as_float((127 + 7 * d) << 23)
-                                                   : __int_as_float((127 + ACC_SHIFT) << 23);
-                const int shift = reg < REGIONS - 1 ? ACC_SHIFT - 7 * d : 0;
+                for (int reg = 0; reg < NREG; ++reg) {
+                    // region reg holds diagonal d = reg + 2 (multiples of 2^-7d, exact), or the
+                    // rounded sum of d >= 7 for the last region
+                    const int d = reg + 2;
+                    const float up = reg < NREG - 1 ? __int_as_float((127 + 7 * d) << 23)
+                                                    : __int_as_float((127 + ACC_SHIFT) << 23);
+                    const int shift = reg < NREG - 1 ? ACC_SHIFT - 7 * d : 0;
+#pragma unroll
+                    for (int c0 = 0; c0 < NT; c0 += 16) {
+                        float v[16];
+                        tmem_ld16(lane_base + reg * NT + c0, v);
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            acc[c0 + i] += (long long)__float2int_rn(v[i] * up) << shift;
+                    }
+                }
+            } else {
+                // one rounded FP32 sum over the whole K: sum < 2^13, kept at 2^-40 resolution
 #pragma unroll
                 for (int c0 = 0; c0 < NT; c0 += 16) {
                     float v[16];
-                    tmem_ld16(lane_base + reg * NT + c0, v);
+                    tmem_ld16(lane_base + c0, v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i)
-                        acc[c0 + i] += (long long)__float2int_rn(v[i] * up) << shift;
+                    for (int i = 0; i < 16; ++i) acc[c0 + i] = __float2ll_rn(v[i] * 0x1p40f);
                 }
             }
             tc_fence_before();
@@ -449,7 +467,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tbase, TMEM_COLS);
+    if (warp == 0) tmem_dealloc(tbase, NCOLS);
     if (!ok) return;
 
     const int row = row0 + tid;
@@ -462,7 +480,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
         double v[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-            v[q] = (c0 + q < N) ? i64_scaled(acc[4 * g + q], er + eB[c0 + q] - ACC_SHIFT) : 0.0;
+            v[q] = (c0 + q < N) ? i64_scaled(acc[4 * g + q], er + eB[c0 + q] - SHIFT) : 0.0;
         if (SPLIT) {
             double *pp = p.part + ((int64_t)blockIdx.y * M + row) * N + c0;
 #pragma unroll
@@ -498,17 +516,44 @@ cudaError_t prepare(Kern k) {
     return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
+template <int NSL>
+cudaError_t prepare_all() {
+    cudaError_t e;
+    if ((e = prepare(k_tc_gemm<EPI_STORE, false, false, NSL>)) != cudaSuccess) return e;
+    if ((e = prepare(k_tc_gemm<EPI_STORE, true, false, NSL>)) != cudaSuccess) return e;
+    if ((e = prepare(k_tc_gemm<EPI_SOLVE, false, false, NSL>)) != cudaSuccess) return e;
+    if ((e = prepare(k_tc_gemm<EPI_ALIAS, false, false, NSL>)) != cudaSuccess) return e;
+    if ((e = prepare(k_tc_gemm<EPI_STORE, false, true, NSL>)) != cudaSuccess) return e;
+    if ((e = prepare(k_tc_gemm<EPI_SOLVE, false, true, NSL>)) != cudaSuccess) return e;
+    return prepare(k_tc_gemm<EPI_ALIAS, false, true, NSL>);
+}
+
+template <bool SPLIT, int NSL>
+cudaError_t launch_tc(int epi, dim3 grid, const TcArgs &p, cudaStream_t s) {
+    switch (epi) {
+        case EPI_STORE: k_tc_gemm<EPI_STORE, false, SPLIT, NSL><<<grid, 128, SMEM_BYTES, s>>>(p); break;
+        case EPI_SOLVE: k_tc_gemm<EPI_SOLVE, false, SPLIT, NSL><<<grid, 128, SMEM_BYTES, s>>>(p); break;
+        case EPI_ALIAS: k_tc_gemm<EPI_ALIAS, false, SPLIT, NSL><<<grid, 128, SMEM_BYTES, s>>>(p); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <bool SPLIT>
+cudaError_t launch_tc_nsl(int nsl, int epi, dim3 grid, const TcArgs &p, cudaStream_t s) {
+    if (nsl == S) return launch_tc<SPLIT, S>(epi, grid, p, s);
+    if (nsl == 2) return launch_tc<SPLIT, 2>(epi, grid, p, s);
+    if (nsl == 1) return launch_tc<SPLIT, 1>(epi, grid, p, s);
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 cudaError_t tc_prepare_kernels() {
     cudaError_t e;
-    if ((e = prepare(k_tc_gemm<EPI_STORE, false, false>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_STORE, true, false>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_SOLVE, false, false>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_ALIAS, false, false>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_STORE, false, true>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_SOLVE, false, true>)) != cudaSuccess) return e;
-    return prepare(k_tc_gemm<EPI_ALIAS, false, true>);
+    if ((e = prepare_all<S>()) != cudaSuccess) return e;
+    if ((e = prepare_all<2>()) != cudaSuccess) return e;
+    return prepare_all<1>();
 }
 
 cudaError_t tc_slice_rows(const double *X, int64_t ld, int rows, int K, int kp, __nv_bfloat16 *out,
@@ -542,7 +587,7 @@ cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t
 
 cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K, int epi,
                     const TcEpilogue &ep, int *status, cudaStream_t s, double *part,
-                    int64_t part_cap, int64_t *launches) {
+                    int64_t part_cap, int64_t *launches, int nsl) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     TcArgs p{};
     p.A = a.data; p.eA = a.expo; p.as = a.slice_stride; p.akp = a.kp;
@@ -561,25 +606,9 @@ cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K,
         splits = (int)cdiv(K, p.kchunk);
     }
     if (launches) *launches += splits > 1 ? 2 : 1;
-    if (splits <= 1) {
-        const unsigned grid = (unsigned)tiles;
-        switch (epi) {
-            case EPI_STORE: k_tc_gemm<EPI_STORE, false, false><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-            case EPI_SOLVE: k_tc_gemm<EPI_SOLVE, false, false><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-            case EPI_ALIAS: k_tc_gemm<EPI_ALIAS, false, false><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
+    if (splits <= 1) return launch_tc_nsl<false>(nsl, epi, dim3((unsigned)tiles), p, s);
     p.part = part;
-    const dim3 grid((unsigned)tiles, splits);
-    switch (epi) {
-        case EPI_STORE: k_tc_gemm<EPI_STORE, false, true><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-        case EPI_SOLVE: k_tc_gemm<EPI_SOLVE, false, true><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-        case EPI_ALIAS: k_tc_gemm<EPI_ALIAS, false, true><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
-    }
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_tc_nsl<true>(nsl, epi, dim3((unsigned)tiles, splits), p, s);
     if (e != cudaSuccess) return e;
     const int64_t work = (int64_t)M * cdiv(N, 4);
     const unsigned rg = (unsigned)cdiv(work, 256);
@@ -599,7 +628,7 @@ cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *p
     p.Gt = Gt; p.status = status;
     p.epi = EpiArgs{nullptr, p.N, nullptr, 0, L, p.N, nullptr, nullptr};
     const int64_t grid = (int64_t)L * cdiv(L, MT) * cdiv(p.N, NT);
-    k_tc_gemm<EPI_STORE, true, false><<<(unsigned)grid, 128, SMEM_BYTES, s>>>(p);
+    k_tc_gemm<EPI_STORE, true, false, S><<<(unsigned)grid, 128, SMEM_BYTES, s>>>(p);
     return cudaGetLastError();
 }
 

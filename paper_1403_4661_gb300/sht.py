@@ -23,14 +23,17 @@ SHT_STATUS = {0: "SHT_OK", 1: "SHT_ERR_INVALID_ARG", 2: "SHT_ERR_UNSUPPORTED", 3
               4: "SHT_ERR_CUDA", 5: "SHT_ERR_NOT_CONVERGED", 6: "SHT_ERR_TIMEOUT"}
 SHT_F64 = 0
 SHT_F64_TENSOR = 1
-DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR}
+SHT_BF16_REFINED = 2
+SHT_BF16X2_REFINED = 3
+DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR, "bf16_refined": SHT_BF16_REFINED,
+          "bf16x2_refined": SHT_BF16X2_REFINED}
 SHT_ORDER_GREEDY = 0
 SHT_ORDER_SIMPLE = 1
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
             "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
-            "sht_forward_noalloc", "sht_plan_check"]
+            "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement"]
 STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
 
 
@@ -44,7 +47,8 @@ class ShtInfo(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int), ("dtype", ctypes.c_int), ("table_bytes", ctypes.c_uint64),
                 ("workspace_bytes", ctypes.c_uint64), ("workspace_batch", ctypes.c_int64),
                 ("plan_seconds", ctypes.c_double), ("order_seconds", ctypes.c_double),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("refine_iterations", ctypes.c_int),
+                ("refine_last_update", ctypes.c_double)]
 
 
 _lib = None
@@ -76,6 +80,7 @@ def load_library(path=LIB_PATH):
     lib.sht_status_string.argtypes = [ctypes.c_int]
     lib.sht_status_string.restype = ctypes.c_char_p
     lib.sht_plan_check.argtypes = [P]
+    lib.sht_plan_set_refinement.argtypes = [P, ctypes.c_int, ctypes.c_double]
     lib.sht_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.sht_plan_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.sht_last_error_message.argtypes = []
@@ -139,6 +144,10 @@ def sht_get_info(h):
     info = ShtInfo()
     _check(load_library().sht_get_info(h, ctypes.byref(info)))
     return {f: getattr(info, f) for f, _ in ShtInfo._fields_}
+
+
+def sht_plan_set_refinement(h, max_iters, tol):
+    _check(load_library().sht_plan_set_refinement(h, int(max_iters), float(tol)))
 
 
 def sht_plan_check(h):
@@ -248,6 +257,10 @@ class Plan:
 
     def info(self):
         return sht_get_info(self.handle)
+
+    def set_refinement(self, max_iters=10, tol=1e-11):
+        """Iteration control of refined plans (tol = 0: fixed iterations, no synchronisation)."""
+        sht_plan_set_refinement(self.handle, max_iters, tol)
 
     def check(self):
         """Synchronise and raise if a bounded device wait gave up since the last check."""

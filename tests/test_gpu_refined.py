@@ -1,0 +1,98 @@
+"""Refined forward transforms (SHT_BF16_REFINED, SHT_BF16X2_REFINED): low-precision tensor-core
+contractions, float64-accurate residual, against the oracle.  Tolerance 1e-10 (refined forms)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import sht as osht
+from paper_1403_4661_gb300 import synth
+from tests.helpers import oracle_thetas, tol_samples
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1403_4661_gb300 import build
+    build.build()
+
+
+def _plan(L, dtype, iters=30, tol=1e-11):
+    from paper_1403_4661_gb300.sht import Plan
+    p = Plan(L, theta=oracle_thetas(L), dtype=dtype)
+    p.set_refinement(iters, tol)
+    return p
+
+
+def _gpu(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
+
+
+@pytest.mark.parametrize("dtype", ["bf16x2_refined", "bf16_refined"])
+@pytest.mark.parametrize("L,B", [(3, 1), (16, 2), (64, 2), (129, 1)])
+def test_refined_forward_matches_oracle(dtype, L, B):
+    th = oracle_thetas(L)
+    s = synth.uniform_samples(L, B, 700 + L)
+    ref = osht.forward(s, L, th)
+    p = _plan(L, dtype)
+    got = p.forward(_gpu(s)).cpu().numpy()
+    p.check()
+    assert np.abs(got - ref).max() <= 1e-10
+    assert 1 <= p.info()["refine_iterations"] <= 30
+
+
+def test_refined_inverse_is_float64_accurate():
+    L, B = 100, 2
+    th = oracle_thetas(L)
+    c = synth.uniform_coeffs(L, B, 3)
+    ref = osht.inverse(c, L, th)
+    got = _plan(L, "bf16x2_refined").inverse(_gpu(c)).cpu().numpy()
+    assert np.abs(got - ref).max() <= tol_samples(ref)
+
+
+def test_not_converged_is_reported():
+    from paper_1403_4661_gb300.sht import SHTError
+    L = 64
+    p = _plan(L, "bf16_refined", iters=1, tol=1e-300)
+    s = _gpu(synth.uniform_samples(L, 1, 4))
+    with pytest.raises(SHTError) as ei:
+        p.forward(s)
+    assert ei.value.status == 5  # SHT_ERR_NOT_CONVERGED
+    assert p.info()["refine_iterations"] == 1
+
+
+def test_fixed_iterations_capture_in_a_graph():
+    L, B = 80, 2
+    p = _plan(L, "bf16x2_refined", iters=4, tol=0.0)
+    p.reserve(B)
+    s = _gpu(synth.uniform_samples(L, B, 5))
+    c = torch.empty_like(s)
+    p.forward(s, out=c)
+    ref = c.clone()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            p.forward(s, out=c)
+    torch.cuda.current_stream().wait_stream(side)
+    c.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(c, ref)
+    th = oracle_thetas(L)
+    assert np.abs(ref.cpu().numpy() - osht.forward(s.cpu().numpy(), L, th)).max() <= 1e-10
+
+
+def test_refined_full_size_round_trip():
+    """BF16x2 refinement at the full size (single-slice BF16 does not converge at L = 1024: its
+    low-precision forward is too far from the inverse of A for the iteration to contract)."""
+    L, B, dtype = 1024, 64, "bf16x2_refined"
+    p = _plan(L, dtype)
+    c = _gpu(synth.decaying_coeffs(L, B, 7))
+    c2 = p.forward(p.inverse(c))
+    p.check()
+    info = p.info()
+    print(dtype, "iterations", info["refine_iterations"], "last update", info["refine_last_update"])
+    assert (c2 - c).abs().max().item() <= 1e-10
