@@ -32,16 +32,11 @@ namespace {
 constexpr int kMaxL = 2048;           // longest ring 4095 -> Bluestein length 8192 in shared memory
 constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring kernels
 
-void free_workspaces(sht_plan_t p) {
-    cudaFree(p->ws_a); cudaFree(p->ws_b); cudaFree(p->ws_g); cudaFree(p->ws_part);
-    p->ws_a = p->ws_b = p->ws_g = p->ws_part = nullptr;
-    cudaFree(p->ws_xS); cudaFree(p->ws_wS); cudaFree(p->ws_xE); cudaFree(p->ws_wE);
-    p->ws_xS = p->ws_wS = nullptr;
-    p->ws_xE = p->ws_wE = nullptr;
-    cudaFree(p->ws_r); cudaFree(p->ws_dx);
-    p->ws_r = p->ws_dx = nullptr;
-    p->ws_batch = 0;
-    p->ws_bytes = 0;
+void free_ws(Workspace &w) {
+    cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
+    cudaFree(w.xS); cudaFree(w.wS); cudaFree(w.xE); cudaFree(w.wE);
+    cudaFree(w.r); cudaFree(w.dx);
+    w = Workspace{};
 }
 
 void destroy(sht_plan_t p) {
@@ -56,54 +51,50 @@ void destroy(sht_plan_t p) {
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
-    free_workspaces(p);
+    free_ws(p->ws);
     if (dev >= 0 && dev != p->device) cudaSetDevice(dev);
     delete p;
 }
 
-sht_status ensure_workspace(sht_plan_t p, int64_t batch) {
-    if (batch <= p->ws_batch) return SHT_OK;
-    free_workspaces(p);
+// Scratch of one workspace for `batch` signals (grows, never shrinks).
+sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
+    if (batch <= w.batch) return SHT_OK;
+    free_ws(w);
     const size_t L = (size_t)p->L;
-    const size_t a = sizeof(double) * (size_t)rows_total(p->L) * 4 * (size_t)batch;
-    const size_t g = sizeof(double) * L * L * 4 * (size_t)batch;
-    const size_t sp = sizeof(double) * (size_t)kSplitCap * L * 4 * (size_t)batch;
-    cudaError_t e = cudaMalloc(&p->ws_a, a);
-    if (e == cudaSuccess) e = cudaMalloc(&p->ws_b, a);
-    if (e == cudaSuccess) e = cudaMalloc(&p->ws_g, g);
-    if (e == cudaSuccess) e = cudaMalloc(&p->ws_part, sp);
+    const size_t Nc = 4 * (size_t)batch;
+    const size_t a = sizeof(double) * (size_t)rows_total(p->L) * Nc;
+    const size_t g = sizeof(double) * L * L * Nc;
+    const size_t sp = sizeof(double) * (size_t)kSplitCap * L * Nc;
+    cudaError_t e = cudaMalloc(&w.a, a);
+    if (e == cudaSuccess) e = cudaMalloc(&w.b, a);
+    if (e == cudaSuccess) e = cudaMalloc(&w.g, g);
+    if (e == cudaSuccess) e = cudaMalloc(&w.part, sp);
+    uint64_t bytes = 2 * a + g + sp;
+    if (e == cudaSuccess && p->refine_nsl > 0) {
+        const size_t io = sizeof(double2) * L * L * (size_t)batch;
+        e = cudaMalloc(&w.r, io);
+        if (e == cudaSuccess) e = cudaMalloc(&w.dx, io);
+        bytes += 2 * io;
+    }
+    if (e == cudaSuccess && p->dtype != SHT_F64) {
+        const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
+        const size_t wsz = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)((p->L + 7) & ~7);
+        e = cudaMalloc(&w.xS, xs);
+        if (e == cudaSuccess) e = cudaMalloc(&w.xE, sizeof(int) * Nc * L);
+        if (e == cudaSuccess) e = cudaMalloc(&w.wS, wsz);
+        if (e == cudaSuccess) e = cudaMalloc(&w.wE, sizeof(int) * Nc);
+        bytes += xs + wsz + sizeof(int) * Nc * (L + 1);
+    }
     if (e != cudaSuccess) {
-        free_workspaces(p);
+        free_ws(w);
         return cuda_check(e, "workspace allocation");
     }
-    p->ws_batch = batch;
-    p->ws_bytes = 2 * a + g + sp;
-    if (p->refine_nsl > 0) {
-        const size_t io = sizeof(double2) * (size_t)p->L * p->L * (size_t)batch;
-        e = cudaMalloc(&p->ws_r, io);
-        if (e == cudaSuccess) e = cudaMalloc(&p->ws_dx, io);
-        if (e != cudaSuccess) {
-            free_workspaces(p);
-            return cuda_check(e, "workspace allocation");
-        }
-        p->ws_bytes += 2 * io;
-    }
-    if (p->dtype != SHT_F64) {
-        const size_t Nc = 4 * (size_t)batch;
-        const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
-        const size_t ws = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)((p->L + 7) & ~7);
-        e = cudaMalloc(&p->ws_xS, xs);
-        if (e == cudaSuccess) e = cudaMalloc(&p->ws_xE, sizeof(int) * Nc * (size_t)p->L);
-        if (e == cudaSuccess) e = cudaMalloc(&p->ws_wS, ws);
-        if (e == cudaSuccess) e = cudaMalloc(&p->ws_wE, sizeof(int) * Nc);
-        if (e != cudaSuccess) {
-            free_workspaces(p);
-            return cuda_check(e, "workspace allocation");
-        }
-        p->ws_bytes += xs + ws + sizeof(int) * Nc * ((size_t)p->L + 1);
-    }
+    w.batch = batch;
+    w.bytes = bytes;
     return SHT_OK;
 }
+
+sht_status ensure_workspace(sht_plan_t p, int64_t batch) { return alloc_ws(p, p->ws, batch); }
 
 // Slices of the P~ table and of the per-order inverses for SHT_F64_TENSOR plans.
 sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
@@ -256,11 +247,11 @@ sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch
 // Forward transform (Procedure 1 in bin space).  Float64 plans run the float64 kernels; the other
 // plans run the contractions on the tensor cores with `nsl` slices per operand (kTcSlices:
 // float64-accurate; fewer: the low-precision forward of the refinement).
-cudaError_t forward_impl(sht_plan_t p, const double2 *d_samples, double2 *d_coeffs, int64_t batch,
-                         cudaStream_t s, int nsl) {
+cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, double2 *d_coeffs,
+                         int64_t batch, cudaStream_t s, int nsl) {
     const int L = p->L;
     const int64_t Nc = 4 * batch;
-    double *W = p->ws_a, *F = p->ws_b;
+    double *W = w.a, *F = w.b;
     cudaError_t e;
     {
         Span sp(p, SHT_STAGE_RING_DFT, s);
@@ -271,26 +262,26 @@ cudaError_t forward_impl(sht_plan_t p, const double2 *d_samples, double2 *d_coef
         const int64_t cap = (int64_t)kSplitCap * L * Nc;
         for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
             const int n = L - m, kp = (n + 7) & ~7;
-            const TcOperand bins{p->ws_wS, p->ws_wE, Nc * kp, kp};
+            const TcOperand bins{w.wS, w.wE, Nc * kp, kp};
             {   // Eq. (14) on the tensor cores: slices of g_m, then F_m = P_m^{-1} g_m
                 Span sp(p, SHT_STAGE_SOLVE, s);
-                e = tc_slice_cols(W + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
+                e = tc_slice_cols(W + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, w.wS, Nc * kp, w.wE, s);
                 const TcOperand inv{p->piS + (int64_t)kTcSlices * p->pik_off[m], p->piE + rows_off(L, m),
                                     (int64_t)n * kp, kp};
                 const TcEpilogue ep{F + rows_off(L, m) * Nc, Nc, nullptr, m, L, d_coeffs, nullptr};
                 if (e == cudaSuccess)
-                    e = tc_gemm(inv, bins, n, (int)Nc, n, EPI_SOLVE, ep, p->d_status, s, p->ws_part, cap,
+                    e = tc_gemm(inv, bins, n, (int)Nc, n, EPI_SOLVE, ep, p->d_status, s, w.part, cap,
                                 &p->launches, nsl);
                 p->launches += 1;
             }
             if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): rings k < m
                 Span sp(p, SHT_STAGE_ALIAS, s);
-                e = tc_slice_cols(F + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, p->ws_wS, Nc * kp, p->ws_wE, s);
+                e = tc_slice_cols(F + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, w.wS, Nc * kp, w.wE, s);
                 const TcOperand low{p->ptS + (int64_t)kTcSlices * L * p->ptk_off[m], p->ptE + (int64_t)m * L,
                                     (int64_t)L * kp, kp};
                 const TcEpilogue ep{nullptr, Nc, nullptr, m, L, nullptr, W};
                 if (e == cudaSuccess)
-                    e = tc_gemm(low, bins, m, (int)Nc, n, EPI_ALIAS, ep, p->d_status, s, p->ws_part, cap,
+                    e = tc_gemm(low, bins, m, (int)Nc, n, EPI_ALIAS, ep, p->d_status, s, w.part, cap,
                                 &p->launches, nsl);
                 p->launches += 1;
             }
@@ -299,7 +290,7 @@ cudaError_t forward_impl(sht_plan_t p, const double2 *d_samples, double2 *d_coef
     }
     GemmArgs ga{};
     ga.L = L; ga.batch = batch; ga.coeffs = d_coeffs; ga.W = W;
-    ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.part = w.part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
     ga.launches = &p->launches;
     for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
         const int n = L - m;
@@ -319,29 +310,29 @@ cudaError_t forward_impl(sht_plan_t p, const double2 *d_samples, double2 *d_coef
 }
 
 // Inverse transform (Procedure 2), float64-accurate for every plan arithmetic.
-cudaError_t inverse_impl(sht_plan_t p, const double2 *d_coeffs, double2 *d_samples, int64_t batch,
-                         cudaStream_t s) {
+cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, double2 *d_samples,
+                         int64_t batch, cudaStream_t s) {
     const int L = p->L;
     cudaError_t e;
     {
         Span sp(p, SHT_STAGE_LAYOUT, s);
-        e = coeffs_to_orders(L, batch, d_coeffs, p->ws_a, s);
+        e = coeffs_to_orders(L, batch, d_coeffs, w.a, s);
     }
     if (e == cudaSuccess) {  // Eq. (11): G_{+-m}(theta_k) for every order and ring
         Span sp(p, SHT_STAGE_SYNTHESIS, s);
         if (p->dtype != SHT_F64) {
-            e = tc_slice_orders(p->ws_a, L, batch, p->d_ptk_off, p->ws_xS, p->ws_xE, s);
+            e = tc_slice_orders(w.a, L, batch, p->d_ptk_off, w.xS, w.xE, s);
             if (e == cudaSuccess)
-                e = tc_synthesis_all_orders(L, batch, p->ptS, p->ptE, p->d_ptk_off, p->ws_xS, p->ws_xE,
-                                            p->ws_g, p->d_status, s);
+                e = tc_synthesis_all_orders(L, batch, p->ptS, p->ptE, p->d_ptk_off, w.xS, w.xE,
+                                            w.g, p->d_status, s);
             p->launches += 1;
         } else {
-            e = synthesis_all_orders(L, batch, p->pt, p->ws_a, p->ws_g, s);
+            e = synthesis_all_orders(L, batch, p->pt, w.a, w.g, s);
         }
     }
     if (e == cudaSuccess) {  // Eq. (18): fold into ring bins, inverse ring DFTs
         Span sp(p, SHT_STAGE_RING_IDFT, s);
-        e = fold_ring_idft(L, p->dft, p->ws_g, d_samples, batch, s);
+        e = fold_ring_idft(L, p->dft, w.g, d_samples, batch, s);
     }
     p->launches += 2 + ring_launches(L);
     return e;
@@ -354,16 +345,17 @@ cudaError_t inverse_impl(sht_plan_t p, const double2 *d_coeffs, double2 *d_sampl
 // refine_max_iters iterations and never synchronises (capturable in a CUDA graph).
 sht_status refined_forward(sht_plan_t p, const double2 *d_samples, double2 *d_coeffs, int64_t batch,
                            cudaStream_t s) {
+    Workspace &w = p->ws;
     const int64_t n = (int64_t)p->L * p->L * batch;
-    cudaError_t e = forward_impl(p, d_samples, d_coeffs, batch, s, p->refine_nsl);
+    cudaError_t e = forward_impl(p, w, d_samples, d_coeffs, batch, s, p->refine_nsl);
     int it = 0;
     double last = INFINITY;
     bool converged = false;
     for (; it < p->refine_max_iters && e == cudaSuccess; ++it) {
-        e = inverse_impl(p, d_coeffs, p->ws_r, batch, s);
-        if (e == cudaSuccess) e = residual(n, d_samples, p->ws_r, s);
-        if (e == cudaSuccess) e = forward_impl(p, p->ws_r, p->ws_dx, batch, s, p->refine_nsl);
-        if (e == cudaSuccess) e = update_with_max(n, d_coeffs, p->ws_dx, p->d_refine_max, s);
+        e = inverse_impl(p, w, d_coeffs, w.r, batch, s);
+        if (e == cudaSuccess) e = residual(n, d_samples, w.r, s);
+        if (e == cudaSuccess) e = forward_impl(p, w, w.r, w.dx, batch, s, p->refine_nsl);
+        if (e == cudaSuccess) e = update_with_max(n, d_coeffs, w.dx, p->d_refine_max, s);
         p->launches += 2;
         if (e == cudaSuccess && p->refine_tol > 0.0) {
             e = cudaMemcpyAsync(&last, p->d_refine_max, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -462,8 +454,8 @@ sht_status sht_get_info(sht_plan_t p, sht_info *out) {
     out->L = p->L;
     out->dtype = p->dtype;
     out->table_bytes = p->table_bytes;
-    out->workspace_bytes = p->ws_bytes;
-    out->workspace_batch = p->ws_batch;
+    out->workspace_bytes = p->ws.bytes;
+    out->workspace_batch = p->ws.batch;
     out->plan_seconds = p->plan_seconds;
     out->order_seconds = p->order_seconds;
     out->kernel_launches = p->launches;
@@ -525,7 +517,8 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     if (p->refine_nsl > 0) return refined_forward(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s);
-    return cuda_check(forward_impl(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s, kTcSlices),
+    return cuda_check(forward_impl(p, p->ws, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s,
+                                   kTcSlices),
                       "sht_forward");
 }
 
@@ -534,7 +527,7 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     sht_status st = check_io(p, d_coeffs, d_samples, batch);
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
-    return cuda_check(inverse_impl(p, (const double2 *)d_coeffs, (double2 *)d_samples, batch,
+    return cuda_check(inverse_impl(p, p->ws, (const double2 *)d_coeffs, (double2 *)d_samples, batch,
                                    (cudaStream_t)stream),
                       "sht_inverse");
 }
@@ -549,15 +542,15 @@ sht_status sht_inverse_adjoint(sht_plan_t p, const void *d_samples, void *d_coef
     cudaError_t e;
     {
         Span sp(p, SHT_STAGE_RING_DFT, s);
-        e = ring_dft_unfold(L, p->dft, (const double2 *)d_samples, p->ws_g, batch, s);
+        e = ring_dft_unfold(L, p->dft, (const double2 *)d_samples, p->ws.g, batch, s);
     }
     if (e == cudaSuccess) {
         Span sp(p, SHT_STAGE_SYNTHESIS, s);
-        e = analysis_all_orders(L, batch, p->pt, p->ws_g, p->ws_a, s);
+        e = analysis_all_orders(L, batch, p->pt, p->ws.g, p->ws.a, s);
     }
     if (e == cudaSuccess) {
         Span sp(p, SHT_STAGE_LAYOUT, s);
-        e = orders_to_coeffs(L, batch, p->ws_a, (double2 *)d_coeffs, s);
+        e = orders_to_coeffs(L, batch, p->ws.a, (double2 *)d_coeffs, s);
     }
     p->launches += 2 + ring_launches(L);
     return cuda_check(e, "sht_inverse_adjoint");
@@ -571,7 +564,7 @@ sht_status sht_forward_adjoint(sht_plan_t p, const void *d_coeffs, void *d_sampl
     cudaStream_t s = (cudaStream_t)stream;
     const int L = p->L;
     const int64_t Nc = 4 * batch;
-    double *X = p->ws_b, *W = p->ws_a, *U = p->ws_g;
+    double *X = p->ws.b, *W = p->ws.a, *U = p->ws.g;
     cudaError_t e;
     {
         Span sp(p, SHT_STAGE_LAYOUT, s);
@@ -579,7 +572,7 @@ sht_status sht_forward_adjoint(sht_plan_t p, const void *d_coeffs, void *d_sampl
     }
     GemmArgs ga{};
     ga.L = L; ga.batch = batch;
-    ga.part = p->ws_part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.part = p->ws.part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
     ga.launches = &p->launches;
     // reverse of the forward chain: m = 0 .. L-1
     for (int m = 0; m < L && e == cudaSuccess; ++m) {

@@ -68,6 +68,20 @@ struct DftPlan {
     std::vector<int> h_filt_M;
 };
 
+// Per-call device scratch, sized for `batch` signals.
+struct Workspace {
+    int64_t batch = 0;
+    double *a = nullptr;             // W (forward bins) / X (inverse coefficients): rows_total * 4B
+    double *b = nullptr;             // F (forward solved coefficients): rows_total * 4B
+    double *g = nullptr;             // Gt (inverse synthesis): L * L * 4B
+    double *part = nullptr;          // split-K partials: kSplitCap * L * 4B
+    __nv_bfloat16 *xS = nullptr;     // tensor plans: slices of X (all orders)
+    __nv_bfloat16 *wS = nullptr;     // tensor plans: slices of one order's bins / coefficients
+    int *xE = nullptr, *wE = nullptr;
+    double2 *r = nullptr, *dx = nullptr;  // refinement: residual, update
+    uint64_t bytes = 0;
+};
+
 }  // namespace sht
 
 struct sht_plan_s {
@@ -79,12 +93,7 @@ struct sht_plan_s {
     double *pt = nullptr;       // P~ table
     double *pinv = nullptr;     // per-order inverses
     sht::DftPlan dft;
-    // workspaces
-    int64_t ws_batch = 0;
-    double *ws_a = nullptr;     // W (forward bins) / X (inverse coefficients): rows_total * 4B
-    double *ws_b = nullptr;     // F (forward solved coefficients): rows_total * 4B
-    double *ws_g = nullptr;     // Gt (inverse synthesis): L * L * 4B
-    double *ws_part = nullptr;  // split-K partials of the order chain: kSplitCap * L * 4B
+    sht::Workspace ws;    // per-call scratch, grown to the largest batch seen
     uint64_t table_bytes = 0;
     uint64_t ws_bytes = 0;
     double plan_seconds = 0.0;
@@ -96,9 +105,7 @@ struct sht_plan_s {
     int64_t *d_ptk_off = nullptr, *d_pik_off = nullptr;
     std::vector<int64_t> ptk_off, pik_off;
     int *d_status = nullptr;
-    // per-call slices (workspace)
-    __nv_bfloat16 *ws_xS = nullptr, *ws_wS = nullptr;
-    int *ws_xE = nullptr, *ws_wE = nullptr;
+
     // refinement (SHT_BF16_REFINED, SHT_BF16X2_REFINED)
     int refine_nsl = 0;           // slices of the low-precision forward; 0: no refinement
     int refine_max_iters = 10;
@@ -106,7 +113,6 @@ struct sht_plan_s {
     int refine_iters = 0;
     double refine_last = 0.0;
     double *d_refine_max = nullptr;
-    double2 *ws_r = nullptr, *ws_dx = nullptr;
     // stage timing (sht_plan_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
