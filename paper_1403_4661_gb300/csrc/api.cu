@@ -35,7 +35,7 @@ constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring k
 void free_ws(Workspace &w) {
     cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
     cudaFree(w.xS); cudaFree(w.wS); cudaFree(w.xE); cudaFree(w.wE);
-    cudaFree(w.r); cudaFree(w.dx);
+    cudaFree(w.r); cudaFree(w.dx); cudaFree(w.bar);
     w = Workspace{};
 }
 
@@ -83,7 +83,8 @@ sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
         if (e == cudaSuccess) e = cudaMalloc(&w.xE, sizeof(int) * Nc * L);
         if (e == cudaSuccess) e = cudaMalloc(&w.wS, wsz);
         if (e == cudaSuccess) e = cudaMalloc(&w.wE, sizeof(int) * Nc);
-        bytes += xs + wsz + sizeof(int) * Nc * (L + 1);
+        if (e == cudaSuccess) e = cudaMalloc(&w.bar, kChainBarWords * sizeof(unsigned));
+        bytes += xs + wsz + sizeof(int) * Nc * (L + 1) + kChainBarWords * sizeof(unsigned);
     }
     if (e != cudaSuccess) {
         free_ws(w);
@@ -119,7 +120,8 @@ sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
     bytes = pts + pis + sizeof(int) * ((size_t)L * L + rows_total(L)) + 2 * sizeof(int64_t) * (L + 1);
     cudaMemcpyAsync(p->d_ptk_off, p->ptk_off.data(), sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(p->d_pik_off, p->pik_off.data(), sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice, s);
-    if ((e = tc_prepare_kernels()) != cudaSuccess) return cuda_check(e, "tensor-core kernel attributes");
+    if ((e = tc_prepare_kernels()) != cudaSuccess || (e = tc_prepare_chain(&p->chain_grid)) != cudaSuccess)
+        return cuda_check(e, "tensor-core kernel attributes");
     if ((e = tc_slice_table(p->pt, L, false, p->d_ptk_off, p->ptS, p->ptE, s)) != cudaSuccess ||
         (e = tc_slice_table(p->pinv, L, true, p->d_pik_off, p->piS, p->piE, s)) != cudaSuccess)
         return cuda_check(e, "tensor-core table slices");
@@ -259,33 +261,13 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
     }
     p->launches += ring_launches(L);
     if (p->dtype != SHT_F64) {
-        const int64_t cap = (int64_t)kSplitCap * L * Nc;
-        for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
-            const int n = L - m, kp = (n + 7) & ~7;
-            const TcOperand bins{w.wS, w.wE, Nc * kp, kp};
-            {   // Eq. (14) on the tensor cores: slices of g_m, then F_m = P_m^{-1} g_m
-                Span sp(p, SHT_STAGE_SOLVE, s);
-                e = tc_slice_cols(W + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, w.wS, Nc * kp, w.wE, s);
-                const TcOperand inv{p->piS + (int64_t)kTcSlices * p->pik_off[m], p->piE + rows_off(L, m),
-                                    (int64_t)n * kp, kp};
-                const TcEpilogue ep{F + rows_off(L, m) * Nc, Nc, nullptr, m, L, d_coeffs, nullptr};
-                if (e == cudaSuccess)
-                    e = tc_gemm(inv, bins, n, (int)Nc, n, EPI_SOLVE, ep, p->d_status, s, w.part, cap,
-                                &p->launches, nsl);
-                p->launches += 1;
-            }
-            if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): rings k < m
-                Span sp(p, SHT_STAGE_ALIAS, s);
-                e = tc_slice_cols(F + rows_off(L, m) * Nc, Nc, n, (int)Nc, kp, w.wS, Nc * kp, w.wE, s);
-                const TcOperand low{p->ptS + (int64_t)kTcSlices * L * p->ptk_off[m], p->ptE + (int64_t)m * L,
-                                    (int64_t)L * kp, kp};
-                const TcEpilogue ep{nullptr, Nc, nullptr, m, L, nullptr, W};
-                if (e == cudaSuccess)
-                    e = tc_gemm(low, bins, m, (int)Nc, n, EPI_ALIAS, ep, p->d_status, s, w.part, cap,
-                                &p->launches, nsl);
-                p->launches += 1;
-            }
-        }
+        // Eqs. (14)-(16) for every order in one persistent launch (stage span: solve)
+        Span sp(p, SHT_STAGE_SOLVE, s);
+        const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off};
+        if (e == cudaSuccess)
+            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.wS, w.wE, w.part, w.bar, p->d_status, nsl,
+                                 p->chain_grid, s);
+        p->launches += 1;
         return e;
     }
     GemmArgs ga{};

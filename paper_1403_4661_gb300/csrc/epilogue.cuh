@@ -51,16 +51,17 @@ __device__ __forceinline__ void epilogue_row4(const EpiArgs &p, int r, int c0, c
         const int a = alias_bin(m, k);
         const int o = a < 0 ? -a : a;
         double *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
+        // read through L2 (__ldcg): in the persistent chain kernel other SMs updated these bins
         if (a == 0) {
-            w[0] -= v[0] + v[2];
-            w[1] -= v[1] + v[3];
+            w[0] = __ldcg(w) - (v[0] + v[2]);
+            w[1] = __ldcg(w + 1) - (v[1] + v[3]);
         } else {
             const int sp = a > 0 ? 0 : 2;   // slot of bin a  (+o or -o)
             const int sm = 2 - sp;          // slot of bin -a
-            w[sp] -= v[0];
-            w[sp + 1] -= v[1];
-            w[sm] -= v[2];
-            w[sm + 1] -= v[3];
+            w[sp] = __ldcg(w + sp) - v[0];
+            w[sp + 1] = __ldcg(w + sp + 1) - v[1];
+            w[sm] = __ldcg(w + sm) - v[2];
+            w[sm + 1] = __ldcg(w + sm + 1) - v[3];
         }
     }
 }

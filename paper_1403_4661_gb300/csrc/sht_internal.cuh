@@ -78,6 +78,7 @@ struct Workspace {
     __nv_bfloat16 *xS = nullptr;     // tensor plans: slices of X (all orders)
     __nv_bfloat16 *wS = nullptr;     // tensor plans: slices of one order's bins / coefficients
     int *xE = nullptr, *wE = nullptr;
+    unsigned *bar = nullptr;         // tensor plans: grid barrier of the chain kernel
     double2 *r = nullptr, *dx = nullptr;  // refinement: residual, update
     uint64_t bytes = 0;
 };
@@ -107,6 +108,7 @@ struct sht_plan_s {
     int *d_status = nullptr;
 
     // refinement (SHT_BF16_REFINED, SHT_BF16X2_REFINED)
+    int chain_grid = 0;           // CTAs of the persistent order-chain kernel (tensor plans)
     int refine_nsl = 0;           // slices of the low-precision forward; 0: no refinement
     int refine_max_iters = 10;
     double refine_tol = 1e-11;
@@ -226,6 +228,17 @@ cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t
 cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K, int epi,
                     const TcEpilogue &ep, int *status, cudaStream_t s, double *part = nullptr,
                     int64_t part_cap = 0, int64_t *launches = nullptr, int nsl = kTcSlices);
+// The forward's whole order chain (m = L-1 .. 0: solves, alias products) as one persistent
+// cooperative launch of `grid` CTAs (tc_prepare_chain); W holds the ring bins on entry.
+struct ChainTables {
+    const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // device offsets
+    const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;
+};
+constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 128-byte lines
+cudaError_t tc_prepare_chain(int *grid);
+cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
+                             double2 *coeffs, __nv_bfloat16 *bS, int *bE, double *part,
+                             unsigned *bar, int *status, int nsl, int grid, cudaStream_t s);
 cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *ptS, const int *ptE,
                                     const int64_t *kpoff, const __nv_bfloat16 *xS, const int *xE,
                                     double *Gt, int *status, cudaStream_t s);

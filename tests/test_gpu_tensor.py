@@ -99,3 +99,35 @@ def test_tensor_deterministic_and_adjoint():
     lhs = torch.vdot(y.flatten(), p.forward(x).flatten())
     rhs = torch.vdot(p.forward_adjoint(y).flatten(), x.flatten())
     assert abs(lhs - rhs).item() <= 1e-11 * abs(lhs).item()
+
+
+def test_tensor_deterministic_and_graph_capture():
+    """The forward's order chain (one persistent cooperative launch) gives identical results on
+    every call and inside a captured CUDA graph."""
+    L, B = 150, 5
+    p = _plan(L)
+    p.reserve(B)
+    c = _gpu(synth.uniform_coeffs(L, B, 77))
+    s = torch.empty_like(c)
+    c2 = torch.empty_like(c)
+    p.inverse(c, out=s)
+    p.forward(s, out=c2)
+    ref = c2.clone()
+    p.forward(s, out=c2)
+    assert torch.equal(c2, ref)
+    c2.zero_()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            p.inverse(c, out=s)
+            p.forward(s, out=c2)
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(2):
+        c2.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(c2, ref)
+    p.check()
+    assert (ref - c).abs().max().item() <= 1e-11
