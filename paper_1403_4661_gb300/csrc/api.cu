@@ -34,7 +34,7 @@ constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring k
 
 void free_ws(Workspace &w) {
     cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
-    cudaFree(w.xS); cudaFree(w.wS); cudaFree(w.xE); cudaFree(w.wE);
+    cudaFree(w.xS); cudaFree(w.xE);
     cudaFree(w.r); cudaFree(w.dx); cudaFree(w.bar);
     w = Workspace{};
 }
@@ -47,6 +47,7 @@ void destroy(sht_plan_t p) {
     cudaFree(p->d_theta); cudaFree(p->pt); cudaFree(p->pinv);
     cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
     cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
+    cudaFree(p->d_tmaps);
     dft_plan_destroy(p->dft);
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -78,13 +79,11 @@ sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
     }
     if (e == cudaSuccess && p->dtype != SHT_F64) {
         const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
-        const size_t wsz = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)((p->L + 7) & ~7);
+        const size_t words = sizeof(unsigned) * (size_t)tc_chain_words(batch);
         e = cudaMalloc(&w.xS, xs);
         if (e == cudaSuccess) e = cudaMalloc(&w.xE, sizeof(int) * Nc * L);
-        if (e == cudaSuccess) e = cudaMalloc(&w.wS, wsz);
-        if (e == cudaSuccess) e = cudaMalloc(&w.wE, sizeof(int) * Nc);
-        if (e == cudaSuccess) e = cudaMalloc(&w.bar, kChainBarWords * sizeof(unsigned));
-        bytes += xs + wsz + sizeof(int) * Nc * (L + 1) + kChainBarWords * sizeof(unsigned);
+        if (e == cudaSuccess) e = cudaMalloc(&w.bar, words);
+        bytes += xs + sizeof(int) * Nc * L + words;
     }
     if (e != cudaSuccess) {
         free_ws(w);
@@ -125,6 +124,9 @@ sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
     if ((e = tc_slice_table(p->pt, L, false, p->d_ptk_off, p->ptS, p->ptE, s)) != cudaSuccess ||
         (e = tc_slice_table(p->pinv, L, true, p->d_pik_off, p->piS, p->piE, s)) != cudaSuccess)
         return cuda_check(e, "tensor-core table slices");
+    if ((e = tc_table_tensor_maps(L, p->piS, p->pik_off, p->ptS, p->ptk_off, &p->d_tmaps)) != cudaSuccess)
+        return cuda_check(e, "tensor maps of the table slices");
+    bytes += (uint64_t)2 * L * kTensorMapBytes;
     e = cudaStreamSynchronize(s);
     return cuda_check(e, "tensor-core table slices");
 }
@@ -263,10 +265,9 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
     if (p->dtype != SHT_F64) {
         // Eqs. (14)-(16) for every order in one persistent launch (stage span: solve)
         Span sp(p, SHT_STAGE_SOLVE, s);
-        const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off};
+        const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off, p->d_tmaps};
         if (e == cudaSuccess)
-            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.wS, w.wE, w.part, w.bar, p->d_status, nsl,
-                                 p->chain_grid, s);
+            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.bar, p->d_status, nsl, p->chain_grid, s);
         p->launches += 1;
         return e;
     }

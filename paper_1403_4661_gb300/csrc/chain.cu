@@ -7,22 +7,28 @@
 // orders run strictly in sequence; per order the work is two small contractions, n x n and
 // m x n by n x 4B.  As separate launches each order costs several kernel starts, tensor-memory
 // allocations and mostly idle SMs; here one CTA per SM stays resident for the whole chain, keeps
-// its tensor memory and mbarriers, and the steps of an order are phases separated by grid-wide
-// barriers:
-//     slice g_m (float64 -> 8 exact BF16 slices per column)        | barrier
-//     solve tiles x K-splits (tcgen05, as in tc_gemm.cu)           | barrier
-//     [sum of the K-split partials in split order; F_m, f_l^{+-m}] | barrier
-//     slice F_m                                                    | barrier
-//     alias tiles x K-splits                                       | barrier
-//     [sum of the partials; subtract from the bins of rings k < m] | barrier
+// its tensor memory and mbarriers, and the steps of an order are four phases separated by
+// grid-wide barriers:
+//     solve: tiles x K-splits of P_m^{-1} g_m (tcgen05 on exact BF16 slices)      | barrier
+//     sum of the K-split partials in split order -> F_m, f_l^{+-m};
+//         column scales of F_m (atomicMax of the exponent fields)                  | barrier
+//     alias: tiles x K-splits of P~_m(rings k < m) F_m                             | barrier
+//     sum of the partials, subtracted from the bins of rings k < m;
+//         column scales of g_{m-1} (its rows are final now)                        | barrier
+// The right-hand sides are read in float64 and cut into slices while they are staged in shared
+// memory, with the column scales the previous phase gathered; the plan tables (P_m^{-1}, P~) are
+// pre-sliced.
+//
 // The cooperative launch guarantees that every CTA is resident, so the barriers cannot wait on a
 // CTA that never runs.  Every wait is bounded (one second); a CTA that gives up sets the plan's
 // status word and an abort word that every other CTA checks in its barrier waits, so all of them
 // leave the chain promptly and release their tensor memory.  Data written by other SMs in an
 // earlier phase is read through L2 (cp.async.cg, __ldcg), never through a possibly stale L1 line.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "epilogue.cuh"
 #include "sht_internal.cuh"
@@ -42,26 +48,29 @@ struct ChainArgs {
     double2 *coeffs;
     const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // P_m^{-1} slices
     const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;   // P~ slices
-    __nv_bfloat16 *bS; int *bE;      // slices of the current right-hand sides: [S][Nc][kp], [Nc]
     double *part;                    // K-split partials: splits x M x Nc
     unsigned *bar;                   // [0] arrivals, [32] generation, [64] abort: separate 128-byte
-                                     // lines (kChainBarWords, zeroed per launch)
+                                     // lines
+    int *eW, *eF;                    // [2][Nc] largest exponent fields of the columns of g_m, F_m
+                                     // (slot m & 1); all of bar, eW, eF zeroed per launch
+    const unsigned char *tmaps;      // TMA maps of the table slices: order m at 2m (P_m^{-1}) and
+                                     // 2m + 1 (P~ block), kTensorMapBytes each
     int *status;
 };
 
-// One contraction C (M x Nc) = A (M x K, plan slices) B (K x Nc, slices in bS).
+// One contraction C (M x Nc) = A (M x K, plan slices) B (K x Nc, float64, row-major).
 struct Job {
-    const __nv_bfloat16 *A; const int *eA; int64_t as; int kp;
+    const void *tmap; const int *eA; int kp;   // A: TMA map {kp, rows, slices}, row scales
+    const double *B; const int *eB;  // eB: exponent fields of B's columns
     int M, K, tiles_n, tiles, splits, kchunk;
-    bool direct;    // epilogue inside the MMA items (no K-splits, no read-modify-write)
 };
 
 __device__ __forceinline__ int cdiv_i(int a, int b) { return (a + b - 1) / b; }
 
-__device__ Job make_job(const __nv_bfloat16 *A, const int *eA, int64_t as, int kp, int M, int K, int Nc,
-                        bool rmw) {
+__device__ Job make_job(const void *tmap, const int *eA, int kp, const double *B, const int *eB, int M,
+                        int K, int Nc) {
     Job j;
-    j.A = A; j.eA = eA; j.as = as; j.kp = kp; j.M = M; j.K = K;
+    j.tmap = tmap; j.eA = eA; j.kp = kp; j.B = B; j.eB = eB; j.M = M; j.K = K;
     j.tiles_n = cdiv_i(Nc, NT);
     j.tiles = cdiv_i(M, MT) * j.tiles_n;
     j.splits = 1;
@@ -76,9 +85,6 @@ __device__ Job make_job(const __nv_bfloat16 *A, const int *eA, int64_t as, int k
             if (sp > 1) { j.splits = sp; j.kchunk = kc; }
         }
     }
-    // a read-modify-write epilogue (alias bins) always goes through the reduction phase, where
-    // one thread per row group keeps many loads in flight
-    j.direct = j.splits == 1 && !rmw;
     return j;
 }
 
@@ -118,61 +124,39 @@ __device__ bool grid_barrier(const ChainArgs &p, int *s_flag) {
     return *s_flag != 0;
 }
 
-// Slices of the n x Nc float64 block X (row-major) as right-hand sides: one warp per column,
-// scale exponent over the column, zero padding to kp.
-__device__ __noinline__ void slice_phase(const ChainArgs &p, const double *X, int n, int kp) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int Nc = p.Nc;
-    const int64_t sstride = (int64_t)Nc * kp;
-    for (int j = blockIdx.x * (kThreads / 32) + warp; j < Nc; j += (kThreads / 32) * gridDim.x) {
+// Largest exponent field of each column over `rows` rows of the row-major block X (Nc columns)
+// into ef[Nc] (atomicMax).  A quarter of the CTAs take rows c, c + G/4, ..; each thread keeps the
+// maximum of its column over eight rows in flight at a time, so each column sees G/4 atomics.
+__device__ void column_fields(const ChainArgs &p, const double *X, int rows, int *ef) {
+    const int Nc = p.Nc, C = max(1, (int)gridDim.x / 4);
+    if ((int)blockIdx.x >= C) return;
+    for (int j = threadIdx.x; j < Nc; j += kThreads) {
         int mf = 0;
-        for (int k0 = lane; k0 < n; k0 += 32 * 8) {
+        for (int r0 = blockIdx.x; r0 < rows; r0 += 8 * C) {
             double x[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const int k = k0 + 32 * u;
-                x[u] = k < n ? __ldcg(X + (int64_t)k * Nc + j) : 0.0;
+                const int r = r0 + u * C;
+                x[u] = r < rows ? __ldcg(X + (int64_t)r * Nc + j) : 0.0;
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) mf = max(mf, exp_field(x[u]));
         }
-        for (int o = 16; o > 0; o >>= 1) mf = max(mf, __shfl_xor_sync(0xffffffffu, mf, o));
-        const int e = scale_from_field(mf);
-        if (lane == 0) p.bE[j] = e;
-        __nv_bfloat16 *out = p.bS + (int64_t)j * kp;
-        for (int k0 = lane; k0 < kp; k0 += 32 * 4) {
-            double x[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = k0 + 32 * u;
-                x[u] = k < n ? __ldcg(X + (int64_t)k * Nc + j) : 0.0;   // rows n..kp-1: zero padding
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int k = k0 + 32 * u;
-                if (k >= kp) break;
-                __nv_bfloat16 sl[S];
-                split_value(x[u], e, sl);
-#pragma unroll
-                for (int s = 0; s < S; ++s) out[s * sstride + k] = sl[s];
-            }
-        }
+        if (mf > 0) atomicMax(ef + j, mf);
     }
 }
 
-// The contraction's items (output tile, K-split), one per CTA and round.  Without K-splits the
-// epilogue runs here; with them each item stores its float64 partial.  `ok` turns false (for the
-// whole CTA) when an mbarrier wait gives up.
-template <int EPI, int NSL>
-__device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, const EpiArgs &epi, uint32_t tbase,
-                          unsigned char *smem, uint64_t *mbar, uint32_t uses[2], bool &ok) {
+// The contraction's items (output tile, K-split), one per CTA and round; each stores its float64
+// partial.  `ok` turns false (for the whole CTA) when an mbarrier wait gives up.
+template <int NSL>
+__device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32_t tbase,
+                                       unsigned char *smem, uint64_t *mbar, uint64_t *full,
+                                       uint32_t uses[2], uint32_t fills[2], bool &ok) {
     constexpr bool EXACT = NSL == S;
     constexpr int NREG = EXACT ? REGIONS : 1;
     constexpr int SHIFT = EXACT ? ACC_SHIFT : 40;
     const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
-    const int Nc = p.Nc, kp = jb.kp, M = jb.M;
-    const __nv_bfloat16 *A = jb.A, *B = p.bS;
-    const int64_t as = jb.as, bs = (int64_t)Nc * kp;
+    const int Nc = p.Nc, M = jb.M;
     const int items = jb.tiles * jb.splits;
     __shared__ int s_eb[NT];   // scale exponents of the tile's B columns
     for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
@@ -181,26 +165,43 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
         const int row0 = tm * MT, col0 = tn * NT;
         const int kbeg = y * jb.kchunk, kend = min(jb.K, kbeg + jb.kchunk);
         __syncthreads();   // the previous item's epilogue is done with s_eb
-        if (tid < NT) s_eb[tid] = col0 + tid < Nc ? __ldcg(p.bE + col0 + tid) : 0;
+        if (tid < NT) s_eb[tid] = col0 + tid < Nc ? scale_from_field(__ldcg(jb.eB + col0 + tid)) : 0;
+        __syncthreads();
 
+        // k-block kb into stage st: the A slices (all S of them, 128 rows x 32 K, 64-byte
+        // swizzled; zero beyond the table) by one TMA load; B read in float64 (rows >= kend as
+        // zero) and sliced here, thread = column j, row pairs (2i, 2i + 1), i = h, h + 4, ..
         auto load = [&](int kb, int st) {
             const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
             const int kbase = kb * KB;
-            for (int idx = tid; idx < NSL * MT * 4; idx += kThreads) {
-                const int j = idx & 3, r = (idx >> 2) & (MT - 1), s = idx >> 9;
-                const int row = row0 + r, kc = kbase + 8 * j;
-                const bool in = row < M && kc < kp;
-                const __nv_bfloat16 *src = in ? A + s * as + (int64_t)row * kp + kc : A;
-                cp_async16(sa + s * (MT * KB * 2) + j * (MT * 16) + (r >> 3) * 128 + (r & 7) * 16, src, in ? 16 : 0);
+            if (tid == 0) {
+                mbar_expect_tx(smem_u32(&full[st]), A_STAGE);
+                tma_load_3d(sa, jb.tmap, kbase, row0, 0, smem_u32(&full[st]));
             }
-            for (int idx = tid; idx < NSL * NT * 4; idx += kThreads) {
-                const int j = idx & 3, r = (idx >> 2) & (NT - 1), s = idx >> 8;
-                const int row = col0 + r, kc = kbase + 8 * j;
-                const bool in = row < Nc && kc < kp;
-                const __nv_bfloat16 *src = in ? B + s * bs + (int64_t)row * kp + kc : B;
-                cp_async16(sb + s * (NT * KB * 2) + j * (NT * 16) + (r >> 3) * 128 + (r & 7) * 16, src, in ? 16 : 0);
+            fills[st] += 1;
+            const int j = tid & (NT - 1), h = tid >> 6, col = col0 + j;
+            const int e = s_eb[j];
+            double x[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int k = kbase + 2 * (h + 4 * (i >> 1)) + (i & 1);
+                x[i] = (col < Nc && k < kend) ? __ldcg(jb.B + (int64_t)k * Nc + col) : 0.0;
             }
-            cp_async_commit();
+            const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int kk = 2 * (h + 4 * q);
+                __nv_bfloat16 lo[S], hi[S];
+                split_value(x[2 * q], e, lo);
+                split_value(x[2 * q + 1], e, hi);
+                const uint32_t a = cb + (kk >> 3) * (NT * 16) + (kk & 7) * 2;
+#pragma unroll
+                for (int s = 0; s < NSL; ++s)
+                    asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a + s * (NT * KB * 2)),
+                                 "r"((uint32_t)__bfloat16_as_ushort(lo[s]) |
+                                     ((uint32_t)__bfloat16_as_ushort(hi[s]) << 16))
+                                 : "memory");
+            }
         };
 
         long long acc[kCols];   // columns half * kCols .. of row quarter * 32 + lane
@@ -208,33 +209,30 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
         for (int c = 0; c < kCols; ++c) acc[c] = 0;
         const int kb0 = kbeg / KB, nkb = (kend + KB - 1) / KB;
         load(kb0, 0);
+        fence_proxy_async();
+        __syncthreads();
         for (int kb = kb0; kb < nkb; ++kb) {
             const int st = (kb - kb0) & 1;
-            if (kb + 1 < nkb) {
-                const int ns = st ^ 1;
-                const bool w = uses[ns] == 0 || mbar_wait(smem_u32(&mbar[ns]), (uses[ns] - 1) & 1u);
+            // stage st holds k-block kb once its TMA load has landed: issue its MMAs, then stage the
+            // next block while they run
+            {
+                const bool w = mbar_wait(smem_u32(&full[st]), (fills[st] - 1) & 1u);
                 if (!__syncthreads_and(w)) { ok = false; break; }
-                load(kb + 1, ns);
-                cp_async_wait<1>();
-            } else {
-                cp_async_wait<0>();
             }
-            fence_proxy_async();
-            __syncthreads();
             if (tid == 0) {
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
                 bool fresh[REGIONS] = {false, false, false, false, false, false};
-                for (int h = 0; h < 2; ++h) {
-                    const int kg = kb * KB + 16 * h;
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int kg = kb * KB + 16 * hh;
                     if (kg >= kend) break;
                     if (kg == kbeg || (EXACT && kg % CHUNK == 0))
                         for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
                     for (int s = 1; s <= NSL; ++s)
                         for (int t = 1; s + t <= NSL + 1; ++t) {
                             const int d = s + t, reg = EXACT ? (d <= 6 ? d - 2 : 5) : 0;
-                            const uint64_t ad = sdesc(sa + (s - 1) * (MT * KB * 2) + 2 * h * (MT * 16), MT * 16, 128);
-                            const uint64_t bd = sdesc(sb + (t - 1) * (NT * KB * 2) + 2 * h * (NT * 16), NT * 16, 128);
+                            const uint64_t ad = sdesc_sw64(sa + (s - 1) * (MT * KB * 2) + 32 * hh);
+                            const uint64_t bd = sdesc(sb + (t - 1) * (NT * KB * 2) + 2 * hh * (NT * 16), NT * 16, 128);
                             mma_bf16(tbase + reg * NT, ad, bd, kIdesc, fresh[reg] ? 0u : 1u);
                             fresh[reg] = false;
                         }
@@ -242,8 +240,19 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
                 mma_commit(smem_u32(&mbar[st]));
             }
             uses[st] += 1;
+            if (kb + 1 < nkb) {
+                // the MMAs of k-block kb - 1 read stage ns: wait for them before refilling it;
+                // the vote keeps every thread on the same path if the wait gives up
+                const int ns = st ^ 1;
+                const bool w = uses[ns] == 0 || mbar_wait(smem_u32(&mbar[ns]), (uses[ns] - 1) & 1u);
+                if (!__syncthreads_and(w)) { ok = false; break; }
+                load(kb + 1, ns);
+                fence_proxy_async();
+                __syncthreads();
+            }
             const int kdone = (kb + 1) * KB;
             if ((EXACT && kdone % CHUNK == 0) || kb == nkb - 1) {
+                // the commit of this stage covers every MMA issued so far
                 const bool w = mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u);
                 if (!__syncthreads_and(w)) { ok = false; break; }
                 tc_fence_after();
@@ -251,6 +260,8 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
                 if (EXACT) {
 #pragma unroll
                     for (int reg = 0; reg < NREG; ++reg) {
+                        // region reg holds diagonal d = reg + 2 (multiples of 2^-7d, exact), or
+                        // the rounded sum of d >= 7 for the last region
                         const int d = reg + 2;
                         const float up = reg < NREG - 1 ? __int_as_float((127 + 7 * d) << 23)
                                                         : __int_as_float((127 + ACC_SHIFT) << 23);
@@ -265,6 +276,7 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
                         }
                     }
                 } else {
+                    // one rounded FP32 sum over the whole K-split: kept at 2^-40 resolution
 #pragma unroll
                     for (int c0 = 0; c0 < kCols; c0 += 16) {
                         float v[16];
@@ -277,7 +289,6 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
                 __syncthreads();
             }
         }
-        cp_async_wait<0>();
         if (!ok) break;
 
         const int row = row0 + (warp & 3) * 32 + (tid & 31);
@@ -290,52 +301,97 @@ __device__ __forceinline__ void mma_phase(const ChainArgs &p, const Job &jb, con
                 double v[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) v[q] = i64_scaled(acc[4 * g + q], er + s_eb[cl + q] - SHIFT);
-                if (jb.direct) {
-                    epilogue_row4<EPI>(epi, row, c0, v);
-                } else {
-                    double *pp = p.part + ((int64_t)y * M + row) * Nc + c0;
-                    *reinterpret_cast<double2 *>(pp) = make_double2(v[0], v[1]);
-                    *reinterpret_cast<double2 *>(pp + 2) = make_double2(v[2], v[3]);
-                }
+                double *pp = p.part + ((int64_t)y * M + row) * Nc + c0;
+                *reinterpret_cast<double2 *>(pp) = make_double2(v[0], v[1]);
+                *reinterpret_cast<double2 *>(pp + 2) = make_double2(v[2], v[3]);
                 asm volatile("" ::: "memory");   // one group at a time (register pressure)
             }
         }
     }
 }
 
-// Sum of the K-split partials in split order (deterministic), then the epilogue.
-template <int EPI>
-__device__ __noinline__ void reduce_phase(const ChainArgs &p, const EpiArgs &epi, int M, int splits) {
-    const int Nc = p.Nc, groups = Nc / 4;
-    const int64_t total = (int64_t)M * groups;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-         t += (int64_t)gridDim.x * blockDim.x) {
-        const int r = (int)(t / groups), c0 = 4 * (int)(t - (int64_t)r * groups);
-        // partials in split order, four loads in flight at a time
-        double v[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int y0 = 0; y0 < splits; y0 += 4) {
-            double2 a[4], b[4];
+// Sum of the K-split partials of row r, columns c0..c0+3, in split order (deterministic).
+__device__ __forceinline__ void sum_partials(const ChainArgs &p, int M, int splits, int r, int c0, double v[4]) {
+    const int Nc = p.Nc;
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    for (int y0 = 0; y0 < splits; y0 += 8) {
+        double2 a[8], b[8];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (y0 + u < splits) {
-                    const double2 *pp =
-                        reinterpret_cast<const double2 *>(p.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
-                    a[u] = __ldcg(pp);
-                    b[u] = __ldcg(pp + 1);
-                }
+        for (int u = 0; u < 8; ++u)
+            if (y0 + u < splits) {
+                const double2 *pp = reinterpret_cast<const double2 *>(p.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
+                a[u] = __ldcg(pp);
+                b[u] = __ldcg(pp + 1);
+            }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (y0 + u < splits) { v[0] += a[u].x; v[1] += a[u].y; v[2] += b[u].x; v[3] += b[u].y; }
-        }
-        epilogue_row4<EPI>(epi, r, c0, v);
+        for (int u = 0; u < 8; ++u)
+            if (y0 + u < splits) { v[0] += a[u].x; v[1] += a[u].y; v[2] += b[u].x; v[3] += b[u].y; }
     }
+}
+
+// Solve epilogue: F_m rows and f_l^{+-m}; largest exponent fields of F_m's columns into ef.
+// When the grid's thread count is a multiple of the column groups, every thread of a CTA stays on
+// one group and the CTA's groups are a window of kThreads groups: the maxima are first gathered in
+// shared memory, one global atomicMax per CTA and column.
+__device__ __noinline__ void reduce_solve(const ChainArgs &p, const EpiArgs &epi, int M, int splits, int *ef) {
+    const int groups = p.Nc / 4;
+    const int64_t total = (int64_t)M * groups, T = (int64_t)gridDim.x * kThreads;
+    __shared__ int s_ef[4 * kThreads];
+    const bool windowed = T % groups == 0;
+    const int g0 = (int)(((int64_t)blockIdx.x * kThreads) % groups);
+    const int span = min(groups, kThreads);
+    for (int i = threadIdx.x; i < 4 * kThreads; i += kThreads) s_ef[i] = 0;
+    __syncthreads();
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
+        const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
+        double v[4];
+        sum_partials(p, M, splits, r, 4 * g, v);
+        epilogue_row4<EPI_SOLVE>(epi, r, 4 * g, v);
+        const int w = g - g0 < 0 ? g - g0 + groups : g - g0;   // position in the CTA's window
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int f = exp_field(v[q]);
+            if (f == 0) continue;
+            if (windowed) atomicMax(&s_ef[4 * w + q], f);
+            else atomicMax(ef + 4 * g + q, f);
+        }
+    }
+    __syncthreads();
+    if (windowed)
+        for (int i = threadIdx.x; i < 4 * span; i += kThreads) {
+            const int w = i >> 2, g = g0 + w < groups ? g0 + w : g0 + w - groups;
+            if (s_ef[i] > 0) atomicMax(ef + 4 * g + (i & 3), s_ef[i]);
+        }
+}
+
+// Alias epilogue: subtract from the bins of rings k < m; then the rows of g_{m-1} are final:
+// ring m - 1 (row 0 of block m - 1, just updated here by the thread that wrote it) and rings
+// m .. L-1 (rows 1 ..), whose largest exponent fields go to ef.
+__device__ __noinline__ void reduce_alias(const ChainArgs &p, const EpiArgs &epi, int m, int splits, int *ef) {
+    const int L = p.L, Nc = p.Nc, groups = Nc / 4;
+    const int64_t total = (int64_t)m * groups, T = (int64_t)gridDim.x * kThreads;
+    const double *g1 = p.W + rows_off(L, m - 1) * Nc;   // block m - 1
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
+        const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
+        double v[4];
+        sum_partials(p, m, splits, r, 4 * g, v);
+        epilogue_row4<EPI_ALIAS>(epi, r, 4 * g, v);
+        if (r == m - 1)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int f = exp_field(__ldcg(g1 + 4 * g + q));
+                if (f > 0) atomicMax(ef + 4 * g + q, f);
+            }
+    }
+    column_fields(p, g1 + Nc, L - m, ef);
 }
 
 template <int NSL>
 __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     constexpr uint32_t NCOLS = NSL == S ? TMEM_COLS : 64u;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar[2];   // MMAs of a stage done
+    __shared__ uint64_t full[2];   // TMA load of a stage landed
     __shared__ uint32_t tmem_slot;
     __shared__ int s_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -343,6 +399,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
+        mbar_init(smem_u32(&full[0]), 1);
+        mbar_init(smem_u32(&full[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
@@ -350,45 +408,47 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     tc_fence_after();
     const uint32_t tbase = tmem_slot;
 
-    uint32_t uses[2] = {0u, 0u};
+    uint32_t uses[2] = {0u, 0u}, fills[2] = {0u, 0u};
     bool ok = true, mma_ok = true;
     const int L = p.L, Nc = p.Nc;
-    for (int m = L - 1; m >= 0; --m) {
-        const int n = L - m, kp = (n + 7) & ~7;
+    // column scales of g_{L-1}: the single ring L-1
+    column_fields(p, p.W + rows_off(L, L - 1) * Nc, 1, p.eW + ((L - 1) & 1) * Nc);
+    ok = grid_barrier(p, &s_flag);
+    for (int m = L - 1; m >= 0 && ok; --m) {
+        const int n = L - m, kp = (n + 7) & ~7, sl = m & 1;
+        // slots of order m - 1: no reader until after the next barrier (last read by order m + 1)
+        for (int j = blockIdx.x * kThreads + tid; j < Nc; j += gridDim.x * kThreads) {
+            p.eW[(sl ^ 1) * Nc + j] = 0;
+            p.eF[(sl ^ 1) * Nc + j] = 0;
+        }
         // Eq. (14): F_m = P_m^{-1} g_m
-        slice_phase(p, p.W + rows_off(L, m) * Nc, n, kp);
-        if (!(ok = grid_barrier(p, &s_flag))) break;
-        const Job js = make_job(p.piS + (int64_t)S * p.pik_off[m], p.piE + rows_off(L, m), (int64_t)n * kp,
-                                kp, n, n, Nc, false);
-        const EpiArgs es{p.F + rows_off(L, m) * Nc, Nc, nullptr, m, L, Nc, p.coeffs, nullptr};
-        mma_phase<EPI_SOLVE, NSL>(p, js, es, tbase, smem, mbar, uses, mma_ok);
+        const Job js = make_job(p.tmaps + (size_t)(2 * m) * kTensorMapBytes, p.piE + rows_off(L, m), kp,
+                                p.W + rows_off(L, m) * Nc, p.eW + sl * Nc, n, n, Nc);
+        mma_phase<NSL>(p, js, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
         if (!(ok = grid_barrier(p, &s_flag))) break;
-        if (!js.direct) {
-            reduce_phase<EPI_SOLVE>(p, es, n, js.splits);
-            if (!(ok = grid_barrier(p, &s_flag))) break;
-        }
+        const EpiArgs es{p.F + rows_off(L, m) * Nc, Nc, nullptr, m, L, Nc, p.coeffs, nullptr};
+        reduce_solve(p, es, n, js.splits, p.eF + sl * Nc);
+        if (!(ok = grid_barrier(p, &s_flag))) break;
         if (m == 0) break;
         // Eqs. (15)-(16): orders +-m out of the bins of rings k < m
-        slice_phase(p, p.F + rows_off(L, m) * Nc, n, kp);
-        if (!(ok = grid_barrier(p, &s_flag))) break;
-        const Job ja = make_job(p.ptS + (int64_t)S * L * p.ptk_off[m], p.ptE + (int64_t)m * L, (int64_t)L * kp,
-                                kp, m, n, Nc, true);
-        const EpiArgs ea{nullptr, Nc, nullptr, m, L, Nc, nullptr, p.W};
-        mma_phase<EPI_ALIAS, NSL>(p, ja, ea, tbase, smem, mbar, uses, mma_ok);
+        const Job ja = make_job(p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes, p.ptE + (int64_t)m * L, kp,
+                                p.F + rows_off(L, m) * Nc, p.eF + sl * Nc, m, n, Nc);
+        mma_phase<NSL>(p, ja, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
         if (!(ok = grid_barrier(p, &s_flag))) break;
-        if (!ja.direct) {
-            reduce_phase<EPI_ALIAS>(p, ea, m, ja.splits);
-            if (!(ok = grid_barrier(p, &s_flag))) break;
-        }
+        const EpiArgs ea{nullptr, Nc, nullptr, m, L, Nc, nullptr, p.W};
+        reduce_alias(p, ea, m, ja.splits, p.eW + (sl ^ 1) * Nc);
+        if (!(ok = grid_barrier(p, &s_flag))) break;
     }
     if (!mma_ok) {
-        // let the MMAs in flight finish (bounded) before the tensor memory is released
-        for (int st = 0; st < 2; ++st)
+        // let the TMA loads and MMAs in flight finish (bounded) before the CTA releases its
+        // shared and tensor memory
+        for (int st = 0; st < 2; ++st) {
+            if (fills[st] > 0) mbar_wait(smem_u32(&full[st]), (fills[st] - 1) & 1u);
             if (uses[st] > 0) mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u);
+        }
     }
-    (void)ok;
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tbase, NCOLS);
@@ -411,6 +471,45 @@ cudaError_t launch_chain(const ChainArgs &p, int grid, cudaStream_t s) {
 
 }  // namespace
 
+cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vector<int64_t> &pik_off,
+                                 const __nv_bfloat16 *ptS, const std::vector<int64_t> &ptk_off,
+                                 unsigned char **d_maps) {
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    const Encode encode = reinterpret_cast<Encode>(fn);
+    std::vector<CUtensorMap> maps((size_t)2 * L);
+    for (int m = 0; m < L; ++m) {
+        const int n = L - m;
+        const cuuint64_t kp = (cuuint64_t)((n + 7) & ~7);
+        for (int w = 0; w < 2; ++w) {
+            // w = 0: P_m^{-1} block (n rows, slice stride n kp); w = 1: P~ block (L rows)
+            const cuuint64_t rows = w == 0 ? (cuuint64_t)n : (cuuint64_t)L;
+            const __nv_bfloat16 *base = w == 0 ? piS + (int64_t)S * pik_off[m] : ptS + (int64_t)S * L * ptk_off[m];
+            const cuuint64_t dims[3] = {kp, rows, (cuuint64_t)S};
+            const cuuint64_t strides[2] = {kp * 2, rows * kp * 2};
+            const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)MT, (cuuint32_t)S};
+            const cuuint32_t step[3] = {1, 1, 1};
+            const CUresult r = encode(&maps[(size_t)2 * m + w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
+                                      const_cast<__nv_bfloat16 *>(base), dims, strides, box, step,
+                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        }
+    }
+    const size_t bytes = maps.size() * sizeof(CUtensorMap);
+    if ((e = cudaMalloc(d_maps, bytes)) != cudaSuccess) return e;
+    return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
+}
+
+int64_t tc_chain_words(int64_t batch) { return kChainBarWords + 16 * batch; }
+
 cudaError_t tc_prepare_chain(int *grid) {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_chain<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess ||
@@ -428,15 +527,18 @@ cudaError_t tc_prepare_chain(int *grid) {
 }
 
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, __nv_bfloat16 *bS, int *bE, double *part,
-                             unsigned *bar, int *status, int nsl, int grid, cudaStream_t s) {
+                             double2 *coeffs, double *part, unsigned *words, int *status, int nsl,
+                             int grid, cudaStream_t s) {
     ChainArgs p{};
     p.L = L; p.Nc = (int)(4 * batch);
     p.W = W; p.F = F; p.coeffs = coeffs;
     p.piS = t.piS; p.piE = t.piE; p.pik_off = t.pik_off;
     p.ptS = t.ptS; p.ptE = t.ptE; p.ptk_off = t.ptk_off;
-    p.bS = bS; p.bE = bE; p.part = part; p.bar = bar; p.status = status;
-    cudaError_t e = cudaMemsetAsync(bar, 0, kChainBarWords * sizeof(unsigned), s);
+    p.tmaps = t.tmaps;
+    p.part = part; p.bar = words; p.status = status;
+    p.eW = reinterpret_cast<int *>(words + kChainBarWords);
+    p.eF = p.eW + 2 * p.Nc;
+    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * tc_chain_words(batch), s);
     if (e != cudaSuccess) return e;
     if (nsl == S) return launch_chain<S>(p, grid, s);
     if (nsl == 2) return launch_chain<2>(p, grid, s);

@@ -76,9 +76,8 @@ struct Workspace {
     double *g = nullptr;             // Gt (inverse synthesis): L * L * 4B
     double *part = nullptr;          // split-K partials: kSplitCap * L * 4B
     __nv_bfloat16 *xS = nullptr;     // tensor plans: slices of X (all orders)
-    __nv_bfloat16 *wS = nullptr;     // tensor plans: slices of one order's bins / coefficients
-    int *xE = nullptr, *wE = nullptr;
-    unsigned *bar = nullptr;         // tensor plans: grid barrier of the chain kernel
+    int *xE = nullptr;
+    unsigned *bar = nullptr;         // tensor plans: words of the chain kernel (tc_chain_words)
     double2 *r = nullptr, *dx = nullptr;  // refinement: residual, update
     uint64_t bytes = 0;
 };
@@ -104,6 +103,7 @@ struct sht_plan_s {
     __nv_bfloat16 *ptS = nullptr, *piS = nullptr;
     int *ptE = nullptr, *piE = nullptr;
     int64_t *d_ptk_off = nullptr, *d_pik_off = nullptr;
+    unsigned char *d_tmaps = nullptr;   // TMA maps of the sliced tables (chain kernel)
     std::vector<int64_t> ptk_off, pik_off;
     int *d_status = nullptr;
 
@@ -233,12 +233,22 @@ cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K,
 struct ChainTables {
     const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // device offsets
     const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;
+    const unsigned char *tmaps;   // device: 2 L TMA maps (tc_table_tensor_maps)
 };
+constexpr int kTensorMapBytes = 128;
+// TMA maps of the sliced tables for the chain kernel, order m at 2m (P_m^{-1} block: {kp, n, S})
+// and 2m + 1 (P~ block: {kp, L, S}), boxes of 32 x 128 x S, 64-byte swizzle; written to a new
+// device array *d_maps of 2 L * kTensorMapBytes bytes (the caller frees it).
+cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vector<int64_t> &pik_off,
+                                 const __nv_bfloat16 *ptS, const std::vector<int64_t> &ptk_off,
+                                 unsigned char **d_maps);
 constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 128-byte lines
 cudaError_t tc_prepare_chain(int *grid);
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, __nv_bfloat16 *bS, int *bE, double *part,
-                             unsigned *bar, int *status, int nsl, int grid, cudaStream_t s);
+                             double2 *coeffs, double *part, unsigned *words, int *status, int nsl,
+                             int grid, cudaStream_t s);
+// Device words the chain kernel needs beside W, F and part (barrier, column scales).
+int64_t tc_chain_words(int64_t batch);
 cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *ptS, const int *ptE,
                                     const int64_t *kpoff, const __nv_bfloat16 *xS, const int *xE,
                                     double *Gt, int *status, cudaStream_t s);
