@@ -34,7 +34,7 @@ constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring k
 
 void free_ws(Workspace &w) {
     cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
-    cudaFree(w.xS); cudaFree(w.xE);
+    cudaFree(w.xS); cudaFree(w.xE); cudaFree(w.tmX);
     cudaFree(w.r); cudaFree(w.dx); cudaFree(w.bar);
     w = Workspace{};
 }
@@ -83,7 +83,8 @@ sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
         e = cudaMalloc(&w.xS, xs);
         if (e == cudaSuccess) e = cudaMalloc(&w.xE, sizeof(int) * Nc * L);
         if (e == cudaSuccess) e = cudaMalloc(&w.bar, words);
-        bytes += xs + sizeof(int) * Nc * L + words;
+        if (e == cudaSuccess) e = tc_x_tensor_maps(p->L, batch, w.xS, p->ptk_off, &w.tmX);
+        bytes += xs + sizeof(int) * Nc * L + words + (uint64_t)p->L * kTensorMapBytes;
     }
     if (e != cudaSuccess) {
         free_ws(w);
@@ -306,8 +307,7 @@ cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, do
         if (p->dtype != SHT_F64) {
             e = tc_slice_orders(w.a, L, batch, p->d_ptk_off, w.xS, w.xE, s);
             if (e == cudaSuccess)
-                e = tc_synthesis_all_orders(L, batch, p->ptS, p->ptE, p->d_ptk_off, w.xS, w.xE,
-                                            w.g, p->d_status, s);
+                e = tc_synthesis_all_orders(L, batch, p->ptE, p->d_tmaps, w.xE, w.tmX, w.g, p->d_status, s);
             p->launches += 1;
         } else {
             e = synthesis_all_orders(L, batch, p->pt, w.a, w.g, s);

@@ -474,16 +474,6 @@ cudaError_t launch_chain(const ChainArgs &p, int grid, cudaStream_t s) {
 cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vector<int64_t> &pik_off,
                                  const __nv_bfloat16 *ptS, const std::vector<int64_t> &ptk_off,
                                  unsigned char **d_maps) {
-    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-    static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-    if (e != cudaSuccess) return e;
-    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
-    const Encode encode = reinterpret_cast<Encode>(fn);
     std::vector<CUtensorMap> maps((size_t)2 * L);
     for (int m = 0; m < L; ++m) {
         const int n = L - m;
@@ -495,16 +485,13 @@ cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vec
             const cuuint64_t dims[3] = {kp, rows, (cuuint64_t)S};
             const cuuint64_t strides[2] = {kp * 2, rows * kp * 2};
             const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)MT, (cuuint32_t)S};
-            const cuuint32_t step[3] = {1, 1, 1};
-            const CUresult r = encode(&maps[(size_t)2 * m + w], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3,
-                                      const_cast<__nv_bfloat16 *>(base), dims, strides, box, step,
-                                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+            const cudaError_t e = encode_tiled_map(&maps[(size_t)2 * m + w], base, dims, strides, box);
+            if (e != cudaSuccess) return e;
         }
     }
     const size_t bytes = maps.size() * sizeof(CUtensorMap);
-    if ((e = cudaMalloc(d_maps, bytes)) != cudaSuccess) return e;
+    const cudaError_t e = cudaMalloc(d_maps, bytes);
+    if (e != cudaSuccess) return e;
     return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
 }
 

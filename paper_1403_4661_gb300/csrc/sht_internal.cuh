@@ -77,6 +77,7 @@ struct Workspace {
     double *part = nullptr;          // split-K partials: kSplitCap * L * 4B
     __nv_bfloat16 *xS = nullptr;     // tensor plans: slices of X (all orders)
     int *xE = nullptr;
+    unsigned char *tmX = nullptr;    // tensor plans: TMA maps of the X slices
     unsigned *bar = nullptr;         // tensor plans: words of the chain kernel (tc_chain_words)
     double2 *r = nullptr, *dx = nullptr;  // refinement: residual, update
     uint64_t bytes = 0;
@@ -195,24 +196,7 @@ cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, doub
 // tc_gemm.cu: float64-accurate contractions on the tensor cores from exact BF16 slices
 constexpr int kTcSlices = 8;     // slices per operand
 constexpr int kTcSliceBits = 7;  // bits per slice
-struct TcOperand {               // K-major slices of a real matrix: [slice][rows][kp] BF16
-    const __nv_bfloat16 *data;
-    const int *expo;             // per-row power-of-two scale
-    int64_t slice_stride;        // rows * kp
-    int kp;                      // padded K (multiple of 8)
-};
-struct TcEpilogue {
-    double *C; int64_t ldc;
-    const double *C0;
-    int m, L;
-    double2 *coeffs;
-    double *W;
-};
 cudaError_t tc_prepare_kernels();
-cudaError_t tc_slice_rows(const double *X, int64_t ld, int rows, int K, int kp, __nv_bfloat16 *out,
-                          int64_t sstride, int *expo, cudaStream_t s);
-cudaError_t tc_slice_cols(const double *X, int64_t ld, int K, int cols, int kp, __nv_bfloat16 *out,
-                          int64_t sstride, int *expo, cudaStream_t s);
 constexpr int kNumSMs = 152;
 // Plan tables: slices of every order's P~ block (inverses = false; slice block m at
 // kTcSlices * L * koff[m] elements, exponents at m * L) or P_m^{-1} block (inverses = true; slices
@@ -223,11 +207,6 @@ cudaError_t tc_slice_table(const double *tab, int L, bool inverses, const int64_
 // at m * 4B.
 cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t *koff,
                             __nv_bfloat16 *out, int *expo, cudaStream_t s);
-// C = A B^T (A: M x K slices, B: N x K slices) with an epilogue; split-K over `part` when the
-// output tiles alone cannot fill the SMs.
-cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K, int epi,
-                    const TcEpilogue &ep, int *status, cudaStream_t s, double *part = nullptr,
-                    int64_t part_cap = 0, int64_t *launches = nullptr, int nsl = kTcSlices);
 // The forward's whole order chain (m = L-1 .. 0: solves, alias products) as one persistent
 // cooperative launch of `grid` CTAs (tc_prepare_chain); W holds the ring bins on entry.
 struct ChainTables {
@@ -249,9 +228,14 @@ cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double 
                              int grid, cudaStream_t s);
 // Device words the chain kernel needs beside W, F and part (barrier, column scales).
 int64_t tc_chain_words(int64_t batch);
-cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *ptS, const int *ptE,
-                                    const int64_t *kpoff, const __nv_bfloat16 *xS, const int *xE,
-                                    double *Gt, int *status, cudaStream_t s);
+// TMA maps of the per-call X slices (order m at m: {kp, 4B, S}, boxes 32 x 64 x S), written to a
+// new device array *d_maps of L * kTensorMapBytes bytes (the caller frees it).
+cudaError_t tc_x_tensor_maps(int L, int64_t batch, const __nv_bfloat16 *xS,
+                             const std::vector<int64_t> &ptk_off, unsigned char **d_maps);
+// Eq. (11) for every order in one launch: Gt[m] (L x 4B) = P~_m X_m.
+cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const int *ptE, const unsigned char *tmA,
+                                    const int *xE, const unsigned char *tmB, double *Gt, int *status,
+                                    cudaStream_t s);
 
 // planner.cu: greedy condition-number ordering (indices into the equiangular set)
 sht_status greedy_order(int L, std::vector<int> &order);

@@ -3,6 +3,7 @@
 // Included by the kernels of tc_gemm.cu and chain.cu.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "sht_internal.cuh"
@@ -192,6 +193,27 @@ __device__ __forceinline__ void slice_row_warp(const double *__restrict__ x, int
 #pragma unroll
         for (int s = 0; s < S; ++s) out[s * sstride + k] = sl[s];
     }
+}
+
+// Host: a 3-D BF16 TMA map (dims[0] = K innermost, then rows, then slices), 64-byte swizzled
+// boxes, zero fill outside the tensor.  The encoder comes from the driver through the runtime.
+inline cudaError_t encode_tiled_map(CUtensorMap *map, const __nv_bfloat16 *base, const cuuint64_t dims[3],
+                                    const cuuint64_t strides[2], const cuuint32_t box[3]) {
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static_assert(sizeof(CUtensorMap) == kTensorMapBytes, "tensor map size");
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    const cuuint32_t step[3] = {1, 1, 1};
+    const CUresult r = reinterpret_cast<Encode>(fn)(
+        map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(base), dims, strides, box, step,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 }  // namespace

@@ -17,14 +17,13 @@
 // scale 2^-49.  Dropping the slices beyond S = 8 and the pairs with s + t > 9 leaves an error of
 // order 2^-49 max|A_i| max|B_j| per term, comparable with a float64 dot product.
 //
-// Kernel: one CTA of 4 warps per 128 x 64 output tile; operands staged through shared memory in
-// the canonical no-swizzle K-major layout (8-row x 16-byte core matrices) by cp.async, two
-// stages of 32 K; one thread issues the 36 slice-pair MMAs (M = 128, N = 64, K = 16) per 16 K and
-// commits them to an mbarrier per stage; every wait is bounded (1 s) and reports through a
-// status word.
+// This file: the slicing of the plan tables and of the inverse's coefficients, and the inverse's
+// synthesis contraction (k_synthesis below); the forward's order chain is in chain.cu.
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "epilogue.cuh"
 #include "sht_internal.cuh"
@@ -32,14 +31,6 @@
 
 namespace sht {
 namespace {
-
-// X row-major (rows x K, leading dim ld); one warp per row.
-__global__ void k_slice_rows(const double *__restrict__ X, int64_t ld, int rows, int K, int kp,
-                             __nv_bfloat16 *__restrict__ out, int64_t sstride, int *__restrict__ expo) {
-    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (row >= rows) return;
-    slice_row_warp(X + (int64_t)row * ld, 1, K, kp, out + (int64_t)row * kp, sstride, expo + row);
-}
 
 // Plan tables, every order m = blockIdx.y: the P~ block (L rows, K = L - m) or the P_m^{-1} block
 // (L - m rows); slices of block m at S * koff[m] rows*kp units.
@@ -121,69 +112,46 @@ __global__ void k_slice_cols_orders(const double *__restrict__ X, int L, int Nc,
                      (int64_t)Nc * kp, expo + (int64_t)m * Nc, blockIdx.x * 32);
 }
 
-// ---------------------------------------------------------------- the GEMM
-struct TcArgs {
-    // single problem
-    const __nv_bfloat16 *A; const int *eA; int64_t as; int akp;
-    const __nv_bfloat16 *B; const int *eB; int64_t bs; int bkp;
-    int M, N, K;
-    EpiArgs epi;
-    // grouped over orders (synthesis): per m, A = P~ slices, B = X slices
-    int L;
-    const __nv_bfloat16 *ptS; const int *ptE; const int64_t *kpoff;
-    const __nv_bfloat16 *xS; const int *xE;
-    double *Gt;
+// ---------------------------------------------------------------- the synthesis contraction
+// Every order m in one launch: G_m (L rings x Nc) = P~_m (L x n) X_m (n x Nc), n = L - m, one CTA
+// per 128 x 64 output tile.  Both operands come pre-sliced (plan table, per-call X slices) and are
+// staged by TMA, 64-byte swizzled, 32 K per stage, two stages.  Thread 0 is the producer and the
+// MMA issuer: it waits for a stage's loads, issues its 36 slice-pair MMAs per 16 K, commits them,
+// then refills the other stage once the MMAs that read it are done, so the tensor pipe always has
+// the next block queued.  All 8 warps drain the six TMEM regions into int64 accumulators at the
+// end of every 128-K chunk (warps w, w + 4: lane quarter w % 4, columns 0..31 / 32..63).
+struct SynArgs {
+    int L, Nc;
+    const int *ptE, *xE;                   // row scales of P~ (m * L + k), column scales of X (m * Nc + j)
+    const unsigned char *tmA, *tmB;        // TMA maps: P~ block of order m at (2m + 1), X slices at m
+    double *Gt;                            // order-major G: m * L * Nc
     int *status;
-    // split-K: blockIdx.y selects K range [y * kchunk, (y + 1) * kchunk); float64 partials to part
-    int kchunk;
-    double *part;
 };
 
-// NSL = slices used per operand: kTcSlices for float64-accurate products (exact diagonals,
-// chunked int64 folding), or 1..2 for the low-precision products of the refinement (every pair in
-// one FP32 region over the whole K, converted once at the end).
-template <int EPI, bool GROUPED, bool SPLIT, int NSL>
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
-    constexpr bool EXACT = NSL == S;
-    constexpr int NREG = EXACT ? REGIONS : 1;
-    constexpr uint32_t NCOLS = EXACT ? TMEM_COLS : 64u;
-    constexpr int SHIFT = EXACT ? ACC_SHIFT : 40;
+constexpr int kSynThreads = 256;
+
+__global__ void __launch_bounds__(kSynThreads, 1) k_synthesis(SynArgs p) {
+    constexpr int kCols = NT / 2;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t mbar[2], full[2];
     __shared__ uint32_t tmem_slot;
-    const int tid = threadIdx.x, warp = tid >> 5;
-
-    const __nv_bfloat16 *A = p.A, *B = p.B;
-    const int *eA = p.eA, *eB = p.eB;
-    int64_t as = p.as, bs = p.bs;
-    int akp = p.akp, bkp = p.bkp, M = p.M, N = p.N, K = p.K;
-    EpiArgs epi = p.epi;
-    const int tiles_n = (N + NT - 1) / NT;
-    int64_t tile = blockIdx.x;
-    if (GROUPED) {
-        const int L = p.L;
-        const int64_t per_m = (int64_t)((L + MT - 1) / MT) * tiles_n;
-        const int m = (int)(tile / per_m);
-        tile -= (int64_t)m * per_m;
-        const int n = L - m, kp = (n + 7) & ~7;
-        const int64_t off = p.kpoff[m];
-        A = p.ptS + (int64_t)S * L * off; as = (int64_t)L * kp; akp = kp; eA = p.ptE + (int64_t)m * L;
-        B = p.xS + (int64_t)S * N * off; bs = (int64_t)N * kp; bkp = kp; eB = p.xE + (int64_t)m * N;
-        M = L; K = n;
-        epi.C = p.Gt + (int64_t)m * L * N; epi.ldc = N; epi.m = m;
-    }
-    const int tm = (int)(tile / tiles_n), tn = (int)(tile % tiles_n);
+    const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
+    const int L = p.L, Nc = p.Nc;
+    const int tiles_n = (Nc + NT - 1) / NT;
+    const int per_m = ((L + MT - 1) / MT) * tiles_n;
+    const int m = (int)(blockIdx.x / per_m), tile = (int)(blockIdx.x - (int64_t)m * per_m);
+    const int tm = tile / tiles_n, tn = tile - tm * tiles_n;
     const int row0 = tm * MT, col0 = tn * NT;
-    int kbeg = 0, kend = K;
-    if (SPLIT) {
-        kbeg = blockIdx.y * p.kchunk;   // a multiple of CHUNK
-        kend = min(K, kbeg + p.kchunk);
-    }
+    const int K = L - m, nkb = (K + KB - 1) / KB;
+    const void *tmA = p.tmA + (size_t)(2 * m + 1) * kTensorMapBytes;
+    const void *tmB = p.tmB + (size_t)m * kTensorMapBytes;
 
-    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), NCOLS);
+    if (warp == 0) tmem_alloc(smem_u32(&tmem_slot), TMEM_COLS);
     if (tid == 0) {
-        mbar_init(smem_u32(&mbar[0]), 1);
-        mbar_init(smem_u32(&mbar[1]), 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_u32(&mbar[i]), 1);
+            mbar_init(smem_u32(&full[i]), 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     tc_fence_before();
@@ -191,220 +159,112 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(TcArgs p) {
     tc_fence_after();
     const uint32_t tbase = tmem_slot;
 
-    // stage loader: A slices rows row0.., B slices rows col0.., k-block kb
-    auto load = [&](int kb, int st) {
+    auto load = [&](int kb) {   // thread 0
+        const int st = kb & 1;
         const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
-        const int kbase = kb * KB;
-        for (int idx = tid; idx < NSL * MT * 4; idx += 128) {
-            const int j = idx & 3, r = (idx >> 2) & (MT - 1), s = idx >> 9;
-            const int row = row0 + r, kc = kbase + 8 * j;
-            const bool ok = row < M && kc < akp;
-            const __nv_bfloat16 *src = ok ? A + s * as + (int64_t)row * akp + kc : A;
-            cp_async16(sa + s * (MT * KB * 2) + j * (MT * 16) + (r >> 3) * 128 + (r & 7) * 16, src, ok ? 16 : 0);
-        }
-        for (int idx = tid; idx < NSL * NT * 4; idx += 128) {
-            const int j = idx & 3, r = (idx >> 2) & (NT - 1), s = idx >> 8;
-            const int row = col0 + r, kc = kbase + 8 * j;
-            const bool ok = row < N && kc < bkp;
-            const __nv_bfloat16 *src = ok ? B + s * bs + (int64_t)row * bkp + kc : B;
-            cp_async16(sb + s * (NT * KB * 2) + j * (NT * 16) + (r >> 3) * 128 + (r & 7) * 16, src, ok ? 16 : 0);
-        }
-        cp_async_commit();
+        mbar_expect_tx(smem_u32(&full[st]), A_STAGE + B_STAGE);
+        tma_load_3d(sa, tmA, kb * KB, row0, 0, smem_u32(&full[st]));
+        tma_load_3d(sb, tmB, kb * KB, col0, 0, smem_u32(&full[st]));
     };
 
-    long long acc[NT];  // C * 2^-(eA + eB) * 2^49, exact integer accumulation across chunks
+    long long acc[kCols];
 #pragma unroll
-    for (int c = 0; c < NT; ++c) acc[c] = 0;
-
-    const int kb0 = kbeg / KB, nkb = (kend + KB - 1) / KB;
-    uint32_t uses[2] = {0u, 0u};
-    bool ok = true;
-    if (kb0 < nkb) load(kb0, 0);
-    for (int kb = kb0; kb < nkb && ok; ++kb) {
-        const int st = (kb - kb0) & 1;
-        if (kb + 1 < nkb) {
-            const int ns = st ^ 1;
-            // the MMAs that read stage ns (k-block kb - 1) must be done before it is refilled;
-            // the vote keeps every thread on the same path if the wait gives up
-            const bool w = uses[ns] == 0 || mbar_wait(smem_u32(&mbar[ns]), (uses[ns] - 1) & 1u);
-            if (!__syncthreads_and(w)) { ok = false; break; }
-            load(kb + 1, ns);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
-            bool fresh[REGIONS] = {false, false, false, false, false, false};
-            for (int h = 0; h < 2; ++h) {
-                const int kg = kb * KB + 16 * h;
-                if (kg >= kend) break;
-                if (EXACT ? (kg % CHUNK == 0) : (kg == kbeg))
-                    for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
-                for (int s = 1; s <= NSL; ++s)
-                    for (int t = 1; s + t <= NSL + 1; ++t) {
-                        const int d = s + t, reg = EXACT ? (d <= 6 ? d - 2 : 5) : 0;
-                        const uint64_t ad = sdesc(sa + (s - 1) * (MT * KB * 2) + 2 * h * (MT * 16), MT * 16, 128);
-                        const uint64_t bd = sdesc(sb + (t - 1) * (NT * KB * 2) + 2 * h * (NT * 16), NT * 16, 128);
-                        mma_bf16(tbase + reg * NT, ad, bd, kIdesc, fresh[reg] ? 0u : 1u);
-                        fresh[reg] = false;
-                    }
-            }
-            mma_commit(smem_u32(&mbar[st]));
-        }
-        uses[st] += 1;
-        const int kdone = (kb + 1) * KB;
-        if ((EXACT && kdone % CHUNK == 0) || kb == nkb - 1) {
-            // the commit of this stage covers every MMA issued so far
-            const bool w = mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u);
-            if (!__syncthreads_and(w)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t lane_base = tbase + ((uint32_t)(warp * 32) << 16);
-            if (EXACT) {
-#pragma unroll
-                for (int reg = 0; reg < NREG; ++reg) {
-                    // region reg holds diagonal d = reg + 2 (multiples of 2^-7d, exact), or the
-                    // rounded sum of d >= 7 for the last region
-                    const int d = reg + 2;
-                    const float up = reg < NREG - 1 ? __int_as_float((127 + 7 * d) << 23)
-                                                    : __int_as_float((127 + ACC_SHIFT) << 23);
-                    const int shift = reg < NREG - 1 ? ACC_SHIFT - 7 * d : 0;
-#pragma unroll
-                    for (int c0 = 0; c0 < NT; c0 += 16) {
-                        float v[16];
-                        tmem_ld16(lane_base + reg * NT + c0, v);
-#pragma unroll
-                        for (int i = 0; i < 16; ++i)
-                            acc[c0 + i] += (long long)__float2int_rn(v[i] * up) << shift;
-                    }
+    for (int c = 0; c < kCols; ++c) acc[c] = 0;
+    bool ok0 = true, alive = true;   // thread 0's waits; the CTA's vote
+    int loads = 0, commits = 0;      // thread 0: issued per CTA (stage = index & 1)
+    if (tid == 0) { load(0); ++loads; }
+    for (int kb = 0; kb < nkb; ++kb) {
+        const int st = kb & 1;
+        const uint32_t par = (uint32_t)(kb >> 1) & 1u;   // use kb >> 1 of stage st
+        if (tid == 0 && ok0) {
+            ok0 = mbar_wait(smem_u32(&full[st]), par);
+            if (ok0) {
+                tc_fence_after();
+                const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
+                bool fresh[REGIONS] = {false, false, false, false, false, false};
+                for (int hh = 0; hh < 2; ++hh) {
+                    const int kg = kb * KB + 16 * hh;
+                    if (kg >= K) break;
+                    if (kg % CHUNK == 0)
+                        for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
+                    for (int s = 1; s <= S; ++s)
+                        for (int t = 1; s + t <= S + 1; ++t) {
+                            const int d = s + t, reg = d <= 6 ? d - 2 : 5;
+                            const uint64_t ad = sdesc_sw64(sa + (s - 1) * (MT * KB * 2) + 32 * hh);
+                            const uint64_t bd = sdesc_sw64(sb + (t - 1) * (NT * KB * 2) + 32 * hh);
+                            mma_bf16(tbase + reg * NT, ad, bd, kIdesc, fresh[reg] ? 0u : 1u);
+                            fresh[reg] = false;
+                        }
                 }
-            } else {
-                // one rounded FP32 sum over the whole K: sum < 2^13, kept at 2^-40 resolution
+                mma_commit(smem_u32(&mbar[st]));
+                ++commits;
+                // refill the other stage once the MMAs of block kb - 1 (its last reader) are done
+                if (kb + 1 < nkb) {
+                    if (kb >= 1) ok0 = mbar_wait(smem_u32(&mbar[st ^ 1]), (uint32_t)((kb - 1) >> 1) & 1u);
+                    if (ok0) { load(kb + 1); ++loads; }
+                }
+            }
+        }
+        if (((kb + 1) * KB) % CHUNK == 0 || kb == nkb - 1) {
+            // the commit of block kb covers every MMA issued so far
+            const bool w = mbar_wait(smem_u32(&mbar[st]), par);
+            alive = __syncthreads_and(w && (tid != 0 || ok0));
+            if (!alive) break;
+            tc_fence_after();
+            const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * kCols);
 #pragma unroll
-                for (int c0 = 0; c0 < NT; c0 += 16) {
+            for (int reg = 0; reg < REGIONS; ++reg) {
+                const int d = reg + 2;
+                const float up = reg < REGIONS - 1 ? __int_as_float((127 + 7 * d) << 23)
+                                                   : __int_as_float((127 + ACC_SHIFT) << 23);
+                const int shift = reg < REGIONS - 1 ? ACC_SHIFT - 7 * d : 0;
+#pragma unroll
+                for (int c0 = 0; c0 < kCols; c0 += 16) {
                     float v[16];
-                    tmem_ld16(lane_base + c0, v);
+                    tmem_ld16(lane_base + reg * NT + c0, v);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) acc[c0 + i] = __float2ll_rn(v[i] * 0x1p40f);
+                    for (int i = 0; i < 16; ++i) acc[c0 + i] += (long long)__float2int_rn(v[i] * up) << shift;
                 }
             }
             tc_fence_before();
             __syncthreads();
         }
     }
-    cp_async_wait<0>();
-    if (!ok) {
-        // let the MMAs in flight finish (bounded) before the tensor memory is released
-        for (int st = 0; st < 2; ++st)
-            if (uses[st] > 0) mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u);
-        if (tid == 0) atomicOr(p.status, 1);
+    if (!alive && tid == 0) {
+        // bounded: let the loads and MMAs in flight finish before the memory is released
+        for (int i = max(0, loads - 2); i < loads; ++i) mbar_wait(smem_u32(&full[i & 1]), (uint32_t)(i >> 1) & 1u);
+        for (int i = max(0, commits - 2); i < commits; ++i) mbar_wait(smem_u32(&mbar[i & 1]), (uint32_t)(i >> 1) & 1u);
+        atomicOr(p.status, 1);
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tbase, NCOLS);
-    if (!ok) return;
+    if (warp == 0) tmem_dealloc(tbase, TMEM_COLS);
+    if (!alive) return;
 
-    const int row = row0 + tid;
-    if (row >= M) return;
-    const int er = eA[row];
+    const int row = row0 + (warp & 3) * 32 + (tid & 31);
+    if (row >= L) return;
+    const int er = p.ptE[(int64_t)m * L + row];
+    const int *eB = p.xE + (int64_t)m * Nc;
+    double *C = p.Gt + ((int64_t)m * L + row) * Nc;
 #pragma unroll
-    for (int g = 0; g < NT / 4; ++g) {
-        const int c0 = col0 + 4 * g;
-        if (c0 >= N) break;
+    for (int g = 0; g < kCols / 4; ++g) {
+        const int c0 = col0 + half * kCols + 4 * g;
+        if (c0 >= Nc) break;
         double v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q)
-            v[q] = (c0 + q < N) ? i64_scaled(acc[4 * g + q], er + eB[c0 + q] - SHIFT) : 0.0;
-        if (SPLIT) {
-            double *pp = p.part + ((int64_t)blockIdx.y * M + row) * N + c0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (c0 + q < N) pp[q] = v[q];
-        } else {
-            epilogue_row4<EPI>(epi, row, c0, v);
-        }
+        for (int q = 0; q < 4; ++q) v[q] = i64_scaled(acc[4 * g + q], er + eB[c0 + q] - ACC_SHIFT);
+        *reinterpret_cast<double2 *>(C + c0) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2 *>(C + c0 + 2) = make_double2(v[2], v[3]);
+        asm volatile("" ::: "memory");
     }
-}
-
-// Fixed-order sum of the split-K partials, then the epilogue (deterministic).
-template <int EPI>
-__global__ void k_tc_reduce(EpiArgs e, const double *__restrict__ part, int splits, int M) {
-    const int groups = (e.N + 3) / 4;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (int64_t)M * groups) return;
-    const int r = (int)(t / groups), c0 = 4 * (int)(t - (int64_t)r * groups);
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int s = 0; s < splits; ++s) {
-        const double *pp = part + ((int64_t)s * M + r) * e.N + c0;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (c0 + q < e.N) v[q] += pp[q];
-    }
-    epilogue_row4<EPI>(e, r, c0, v);
 }
 
 int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-template <typename Kern>
-cudaError_t prepare(Kern k) {
-    return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-}
-
-template <int NSL>
-cudaError_t prepare_all() {
-    cudaError_t e;
-    if ((e = prepare(k_tc_gemm<EPI_STORE, false, false, NSL>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_STORE, true, false, NSL>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_SOLVE, false, false, NSL>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_ALIAS, false, false, NSL>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_STORE, false, true, NSL>)) != cudaSuccess) return e;
-    if ((e = prepare(k_tc_gemm<EPI_SOLVE, false, true, NSL>)) != cudaSuccess) return e;
-    return prepare(k_tc_gemm<EPI_ALIAS, false, true, NSL>);
-}
-
-template <bool SPLIT, int NSL>
-cudaError_t launch_tc(int epi, dim3 grid, const TcArgs &p, cudaStream_t s) {
-    switch (epi) {
-        case EPI_STORE: k_tc_gemm<EPI_STORE, false, SPLIT, NSL><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-        case EPI_SOLVE: k_tc_gemm<EPI_SOLVE, false, SPLIT, NSL><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-        case EPI_ALIAS: k_tc_gemm<EPI_ALIAS, false, SPLIT, NSL><<<grid, 128, SMEM_BYTES, s>>>(p); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
-template <bool SPLIT>
-cudaError_t launch_tc_nsl(int nsl, int epi, dim3 grid, const TcArgs &p, cudaStream_t s) {
-    if (nsl == S) return launch_tc<SPLIT, S>(epi, grid, p, s);
-    if (nsl == 2) return launch_tc<SPLIT, 2>(epi, grid, p, s);
-    if (nsl == 1) return launch_tc<SPLIT, 1>(epi, grid, p, s);
-    return cudaErrorInvalidValue;
-}
-
 }  // namespace
 
 cudaError_t tc_prepare_kernels() {
-    cudaError_t e;
-    if ((e = prepare_all<S>()) != cudaSuccess) return e;
-    if ((e = prepare_all<2>()) != cudaSuccess) return e;
-    return prepare_all<1>();
-}
-
-cudaError_t tc_slice_rows(const double *X, int64_t ld, int rows, int K, int kp, __nv_bfloat16 *out,
-                          int64_t sstride, int *expo, cudaStream_t s) {
-    if (rows <= 0) return cudaSuccess;
-    k_slice_rows<<<(unsigned)cdiv(rows, 8), 256, 0, s>>>(X, ld, rows, K, kp, out, sstride, expo);
-    return cudaGetLastError();
-}
-
-cudaError_t tc_slice_cols(const double *X, int64_t ld, int K, int cols, int kp, __nv_bfloat16 *out,
-                          int64_t sstride, int *expo, cudaStream_t s) {
-    if (cols <= 0) return cudaSuccess;
-    k_slice_cols<<<(unsigned)cdiv(cols, 8), 256, 0, s>>>(X, ld, K, cols, kp, out, sstride, expo);
-    return cudaGetLastError();
+    return cudaFuncSetAttribute(k_synthesis, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
 cudaError_t tc_slice_table(const double *tab, int L, bool inverses, const int64_t *koff,
@@ -422,50 +282,32 @@ cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t
     return cudaGetLastError();
 }
 
-cudaError_t tc_gemm(const TcOperand &a, const TcOperand &b, int M, int N, int K, int epi,
-                    const TcEpilogue &ep, int *status, cudaStream_t s, double *part,
-                    int64_t part_cap, int64_t *launches, int nsl) {
-    if (M <= 0 || N <= 0) return cudaSuccess;
-    TcArgs p{};
-    p.A = a.data; p.eA = a.expo; p.as = a.slice_stride; p.akp = a.kp;
-    p.B = b.data; p.eB = b.expo; p.bs = b.slice_stride; p.bkp = b.kp;
-    p.M = M; p.N = N; p.K = K; p.status = status;
-    p.epi = EpiArgs{ep.C, ep.ldc, ep.C0, ep.m, ep.L, N, ep.coeffs, ep.W};
-    const int64_t tiles = cdiv(M, MT) * cdiv(N, NT);
-    // split K over enough blocks to cover the SMs (chunks of CHUNK keep the exact accumulation)
-    int splits = 1;
-    if (part && tiles < kNumSMs) {
-        splits = (int)std::min<int64_t>(std::min<int64_t>(cdiv(kNumSMs, tiles), cdiv(K, CHUNK)), 16);
-        while (splits > 1 && (int64_t)splits * M * N > part_cap) --splits;
+cudaError_t tc_x_tensor_maps(int L, int64_t batch, const __nv_bfloat16 *xS,
+                             const std::vector<int64_t> &ptk_off, unsigned char **d_maps) {
+    const int Nc = (int)(4 * batch);
+    std::vector<CUtensorMap> maps((size_t)L);
+    for (int m = 0; m < L; ++m) {
+        const cuuint64_t kp = (cuuint64_t)(((L - m) + 7) & ~7);
+        const cuuint64_t dims[3] = {kp, (cuuint64_t)Nc, (cuuint64_t)S};
+        const cuuint64_t strides[2] = {kp * 2, (cuuint64_t)Nc * kp * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)NT, (cuuint32_t)S};
+        cudaError_t e = encode_tiled_map(&maps[m], xS + (int64_t)S * Nc * ptk_off[m], dims, strides, box);
+        if (e != cudaSuccess) return e;
     }
-    if (splits > 1) {
-        p.kchunk = (int)(cdiv(cdiv(K, splits), CHUNK) * CHUNK);
-        splits = (int)cdiv(K, p.kchunk);
-    }
-    if (launches) *launches += splits > 1 ? 2 : 1;
-    if (splits <= 1) return launch_tc_nsl<false>(nsl, epi, dim3((unsigned)tiles), p, s);
-    p.part = part;
-    cudaError_t e = launch_tc_nsl<true>(nsl, epi, dim3((unsigned)tiles, splits), p, s);
+    const size_t bytes = maps.size() * sizeof(CUtensorMap);
+    cudaError_t e = cudaMalloc(d_maps, bytes);
     if (e != cudaSuccess) return e;
-    const int64_t work = (int64_t)M * cdiv(N, 4);
-    const unsigned rg = (unsigned)cdiv(work, 256);
-    switch (epi) {
-        case EPI_STORE: k_tc_reduce<EPI_STORE><<<rg, 256, 0, s>>>(p.epi, part, splits, M); break;
-        case EPI_SOLVE: k_tc_reduce<EPI_SOLVE><<<rg, 256, 0, s>>>(p.epi, part, splits, M); break;
-        case EPI_ALIAS: k_tc_reduce<EPI_ALIAS><<<rg, 256, 0, s>>>(p.epi, part, splits, M); break;
-    }
-    return cudaGetLastError();
+    return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
 }
 
-cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const __nv_bfloat16 *ptS, const int *ptE,
-                                    const int64_t *kpoff, const __nv_bfloat16 *xS, const int *xE,
-                                    double *Gt, int *status, cudaStream_t s) {
-    TcArgs p{};
-    p.L = L; p.N = (int)(4 * batch); p.ptS = ptS; p.ptE = ptE; p.kpoff = kpoff; p.xS = xS; p.xE = xE;
-    p.Gt = Gt; p.status = status;
-    p.epi = EpiArgs{nullptr, p.N, nullptr, 0, L, p.N, nullptr, nullptr};
-    const int64_t grid = (int64_t)L * cdiv(L, MT) * cdiv(p.N, NT);
-    k_tc_gemm<EPI_STORE, true, false, S><<<(unsigned)grid, 128, SMEM_BYTES, s>>>(p);
+cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const int *ptE, const unsigned char *tmA,
+                                    const int *xE, const unsigned char *tmB, double *Gt, int *status,
+                                    cudaStream_t s) {
+    SynArgs p{};
+    p.L = L; p.Nc = (int)(4 * batch); p.ptE = ptE; p.xE = xE; p.tmA = tmA; p.tmB = tmB; p.Gt = Gt;
+    p.status = status;
+    const int64_t grid = (int64_t)L * cdiv(L, MT) * cdiv(p.Nc, NT);
+    k_synthesis<<<(unsigned)grid, kSynThreads, SMEM_BYTES, s>>>(p);
     return cudaGetLastError();
 }
 
