@@ -209,8 +209,11 @@ typedef struct {
 
 /* Stages of the transforms, for sht_plan_stage_times. */
 #define SHT_STAGE_RING_DFT   0  /* forward ring DFTs into bins (forward; adjoint of inverse)   */
-#define SHT_STAGE_SOLVE      1  /* per-order solves P_m^{-1} g_m (forward chain, all m)         */
-#define SHT_STAGE_ALIAS      2  /* alias subtractions from lower rings (forward chain, all m)   */
+#define SHT_STAGE_SOLVE      1  /* per-order solves P_m^{-1} g_m (forward chain, all m); for
+                                   tensor plans the whole chain, solves and alias products,
+                                   which runs as one persistent launch                         */
+#define SHT_STAGE_ALIAS      2  /* alias subtractions from lower rings (forward chain, all m;
+                                   float64 plans)                                              */
 #define SHT_STAGE_LAYOUT     3  /* coefficient <-> order-major conversions                      */
 #define SHT_STAGE_SYNTHESIS  4  /* G_m(theta_k) for all m, k (inverse; adjoint: analysis)       */
 #define SHT_STAGE_RING_IDFT  5  /* fold + inverse ring DFTs (inverse; adjoint of forward)       */
