@@ -138,6 +138,27 @@ sht_status sht_inverse(sht_plan_t plan, const void *d_coeffs, void *d_samples, i
                        void *stream);
 
 /*
+ * sht_forward_uneven, sht_inverse_uneven - one transform direction over nsig signals of different
+ *   band-limits (the per-signal transform is the paper's; batching signals of uneven L is ours).
+ *   plans[0..nplans): plans created beforehand on the calling device, one per band-limit (any
+ *   arithmetic).  Signal i (0 <= i < nsig) uses plans[plan_index[i]] and occupies the L^2 complex128
+ *   values (L of that plan; samples ring-major, coefficients at l^2 + l + m as for the batched calls)
+ *   at complex-element offset offsets[i] of both the input and the output array (device, 16-byte
+ *   aligned).  plans, plan_index and offsets are host arrays, read during the call only.  Signals of
+ *   one plan run as one batch: in place when they are consecutive in the order given, otherwise
+ *   gathered into the plan's staging buffers (grown on demand, kept until the plan is destroyed)
+ *   and scattered back by one device-to-device copy per signal.  Stream-ordered; once the staging
+ *   buffers and workspaces have their size (a first call), a call allocates nothing and can be
+ *   captured in a CUDA graph (refined plans with a tolerance synchronise, as in sht_forward).
+ *   Errors: SHT_ERR_INVALID_ARG for an index outside [0, nplans), a negative offset, overlapping
+ *   signals or overlapping input and output; otherwise those of sht_forward / sht_inverse.
+ */
+sht_status sht_forward_uneven(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                              const int64_t *offsets, const void *d_samples, void *d_coeffs, void *stream);
+sht_status sht_inverse_uneven(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                              const int64_t *offsets, const void *d_coeffs, void *d_samples, void *stream);
+
+/*
  * sht_inverse_adjoint - the adjoint A^H of the inverse map A (A[(k,n),(l,m)] = Y_l^m(theta_k,
  *   phi_kn)): coefficients-shaped output from samples-shaped input,
  *   out_l^m = sum_{k,n} P~_l^m(theta_k) e^{-i m phi_kn} y_kn.  Same layouts as sht_forward.

@@ -1,5 +1,6 @@
 // C ABI of libsht (declared in include/sht.h): plans, argument checking, and the launch
 // sequences of the transforms.  All arithmetic runs in the kernels of this directory.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -53,6 +54,7 @@ void destroy(sht_plan_t p) {
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
     free_ws(p->ws);
+    cudaFree(p->stage);
     if (dev >= 0 && dev != p->device) cudaSetDevice(dev);
     delete p;
 }
@@ -354,6 +356,86 @@ sht_status refined_forward(sht_plan_t p, const double2 *d_samples, double2 *d_co
     return SHT_OK;
 }
 
+// One transform direction over signals of different band-limits: group by plan, run each group as
+// one batch, directly when its signals are consecutive in both buffers, else through the plan's
+// staging buffers (one device copy per signal each way).
+sht_status uneven(bool forward, const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                  const int64_t *offsets, const void *d_in, void *d_out, void *stream) {
+    if (nsig < 0 || nplans < 0) return set_error(SHT_ERR_INVALID_ARG, "negative count");
+    if (nsig == 0) return SHT_OK;
+    if (!plans || !plan_index || !offsets || nplans == 0)
+        return set_error(SHT_ERR_INVALID_ARG, "NULL plan, index or offset array");
+    if (!d_in || !d_out) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");
+    if (((uintptr_t)d_in & 15u) || ((uintptr_t)d_out & 15u))
+        return set_error(SHT_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    for (int g = 0; g < nplans; ++g) {
+        sht_status st = check_plan(plans[g]);
+        if (st != SHT_OK) return st;
+    }
+    // signals as intervals [offset, offset + L^2) of complex elements: in range, disjoint
+    std::vector<std::pair<int64_t, int64_t>> iv((size_t)nsig);
+    for (int64_t i = 0; i < nsig; ++i) {
+        const int g = plan_index[i];
+        if (g < 0 || g >= nplans) return set_error(SHT_ERR_INVALID_ARG, "plan index out of range");
+        if (offsets[i] < 0) return set_error(SHT_ERR_INVALID_ARG, "negative offset");
+        const int64_t L = plans[g]->L;
+        iv[(size_t)i] = {offsets[i], offsets[i] + L * L};
+    }
+    std::sort(iv.begin(), iv.end());
+    for (size_t i = 1; i < iv.size(); ++i)
+        if (iv[i].first < iv[i - 1].second) return set_error(SHT_ERR_INVALID_ARG, "signals overlap");
+    const uintptr_t bytes = (uintptr_t)16 * (uintptr_t)iv.back().second;
+    const uintptr_t a = (uintptr_t)d_in, b = (uintptr_t)d_out;
+    if (a < b + bytes && b < a + bytes) return set_error(SHT_ERR_INVALID_ARG, "input and output overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double2 *in = (const double2 *)d_in;
+    double2 *out = (double2 *)d_out;
+    std::vector<int64_t> members;
+    for (int g = 0; g < nplans; ++g) {
+        sht_plan_t p = plans[g];
+        members.clear();
+        for (int64_t i = 0; i < nsig; ++i)
+            if (plan_index[i] == g) members.push_back(i);
+        if (members.empty()) continue;
+        const int64_t L2 = (int64_t)p->L * p->L, nb = (int64_t)members.size();
+        bool run = true;   // consecutive in the order given
+        for (size_t j = 1; j < members.size() && run; ++j)
+            run = offsets[members[j]] == offsets[members[j - 1]] + L2;
+        for (int64_t b0 = 0; b0 < nb; b0 += kMaxBatch) {
+            const int64_t bn = std::min<int64_t>(kMaxBatch, nb - b0);
+            sht_status st;
+            if (run) {
+                const int64_t off = offsets[members[(size_t)b0]];
+                st = forward ? sht_forward(p, in + off, out + off, bn, stream)
+                             : sht_inverse(p, in + off, out + off, bn, stream);
+            } else {
+                if (bn > p->stage_batch) {
+                    cudaFree(p->stage);
+                    p->stage = nullptr;
+                    p->stage_batch = 0;
+                    cudaError_t e = cudaMalloc(&p->stage, sizeof(double2) * 2 * L2 * bn);
+                    if (e != cudaSuccess) return cuda_check(e, "staging buffers");
+                    p->stage_batch = bn;
+                }
+                double2 *si = p->stage, *so = p->stage + L2 * p->stage_batch;
+                for (int64_t j = 0; j < bn; ++j) {
+                    cudaError_t e = cudaMemcpyAsync(si + j * L2, in + offsets[members[(size_t)(b0 + j)]],
+                                                    sizeof(double2) * L2, cudaMemcpyDeviceToDevice, s);
+                    if (e != cudaSuccess) return cuda_check(e, "gather");
+                }
+                st = forward ? sht_forward(p, si, so, bn, stream) : sht_inverse(p, si, so, bn, stream);
+                for (int64_t j = 0; j < bn && st == SHT_OK; ++j) {
+                    cudaError_t e = cudaMemcpyAsync(out + offsets[members[(size_t)(b0 + j)]], so + j * L2,
+                                                    sizeof(double2) * L2, cudaMemcpyDeviceToDevice, s);
+                    if (e != cudaSuccess) return cuda_check(e, "scatter");
+                }
+            }
+            if (st != SHT_OK) return st;
+        }
+    }
+    return SHT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -513,6 +595,16 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     return cuda_check(inverse_impl(p, p->ws, (const double2 *)d_coeffs, (double2 *)d_samples, batch,
                                    (cudaStream_t)stream),
                       "sht_inverse");
+}
+
+sht_status sht_forward_uneven(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                              const int64_t *offsets, const void *d_samples, void *d_coeffs, void *stream) {
+    return uneven(true, plans, nplans, nsig, plan_index, offsets, d_samples, d_coeffs, stream);
+}
+
+sht_status sht_inverse_uneven(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                              const int64_t *offsets, const void *d_coeffs, void *d_samples, void *stream) {
+    return uneven(false, plans, nplans, nsig, plan_index, offsets, d_coeffs, d_samples, stream);
 }
 
 sht_status sht_inverse_adjoint(sht_plan_t p, const void *d_samples, void *d_coeffs, int64_t batch,

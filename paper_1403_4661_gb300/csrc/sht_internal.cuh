@@ -95,6 +95,8 @@ struct sht_plan_s {
     double *pinv = nullptr;     // per-order inverses
     sht::DftPlan dft;
     sht::Workspace ws;    // per-call scratch, grown to the largest batch seen
+    double2 *stage = nullptr;     // uneven batches: gathered inputs, then outputs (stage_batch each)
+    int64_t stage_batch = 0;
     uint64_t table_bytes = 0;
     uint64_t ws_bytes = 0;
     double plan_seconds = 0.0;

@@ -33,7 +33,8 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
-            "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement"]
+            "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement",
+            "sht_forward_uneven", "sht_inverse_uneven"]
 STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
 
 
@@ -81,6 +82,9 @@ def load_library(path=LIB_PATH):
     lib.sht_status_string.restype = ctypes.c_char_p
     lib.sht_plan_check.argtypes = [P]
     lib.sht_plan_set_refinement.argtypes = [P, ctypes.c_int, ctypes.c_double]
+    for name in ("sht_forward_uneven", "sht_inverse_uneven"):
+        getattr(lib, name).argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(i64), P, P, P]
     lib.sht_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.sht_plan_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.sht_last_error_message.argtypes = []
@@ -202,6 +206,37 @@ def sht_inverse(h, L, coeffs, out=None, stream=None):
     y = torch.empty_like(x) if out is None else out
     _call("sht_inverse", h, x, y, x.numel() // (L * L), stream)
     return y
+
+
+def _uneven(name, plans, plan_index, offsets, x, out, stream):
+    """Signals of different band-limits packed in one flat complex128 tensor: signal i uses
+    plans[plan_index[i]] and occupies L^2 values at element offset offsets[i]."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.complex128:
+        raise TypeError("input must be a complex128 CUDA tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x) if out is None else out
+    n = len(plan_index)
+    if len(offsets) != n:
+        raise ValueError("plan_index and offsets differ in length")
+    hs = (ctypes.c_void_p * max(1, len(plans)))(*[pl.handle for pl in plans])
+    idx = (ctypes.c_int * max(1, n))(*[int(i) for i in plan_index])
+    off = (ctypes.c_int64 * max(1, n))(*[int(o) for o in offsets])
+    ends = [int(o) + plans[int(i)].L ** 2 for i, o in zip(plan_index, offsets)]
+    if ends and max(ends) > x.numel():
+        raise ValueError("signals extend past the end of the input")
+    _check(getattr(load_library(), name)(hs, len(plans), n, idx, off, ctypes.c_void_p(x.data_ptr()),
+                                         ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream)))
+    return y
+
+
+def forward_uneven(plans, plan_index, offsets, samples, out=None, stream=None):
+    """Forward SHT of signals of different band-limits in one call (sht_forward_uneven)."""
+    return _uneven("sht_forward_uneven", plans, plan_index, offsets, samples, out, stream)
+
+
+def inverse_uneven(plans, plan_index, offsets, coeffs, out=None, stream=None):
+    """Inverse SHT of signals of different band-limits in one call (sht_inverse_uneven)."""
+    return _uneven("sht_inverse_uneven", plans, plan_index, offsets, coeffs, out, stream)
 
 
 def sht_forward_adjoint(h, L, coeffs, out=None, stream=None):
