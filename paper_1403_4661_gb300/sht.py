@@ -221,7 +221,8 @@ def _uneven(name, plans, plan_index, offsets, x, out, stream):
     hs = (ctypes.c_void_p * max(1, len(plans)))(*[pl.handle for pl in plans])
     idx = (ctypes.c_int * max(1, n))(*[int(i) for i in plan_index])
     off = (ctypes.c_int64 * max(1, n))(*[int(o) for o in offsets])
-    ends = [int(o) + plans[int(i)].L ** 2 for i, o in zip(plan_index, offsets)]
+    # the library validates indices and offsets; here only the extent of the valid signals
+    ends = [int(o) + plans[int(i)].L ** 2 for i, o in zip(plan_index, offsets) if 0 <= int(i) < len(plans)]
     if ends and max(ends) > x.numel():
         raise ValueError("signals extend past the end of the input")
     _check(getattr(load_library(), name)(hs, len(plans), n, idx, off, ctypes.c_void_p(x.data_ptr()),
