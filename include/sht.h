@@ -208,6 +208,16 @@ sht_status sht_forward_noalloc(sht_plan_t plan, const void *d_samples, void *d_c
 sht_status sht_plan_set_refinement(sht_plan_t plan, int max_iters, double tol);
 
 /*
+ * sht_plan_set_wait_limit - limit, in seconds (1e-9 .. 60), of every wait inside the tensor-core
+ *   kernels of the plan on other CTAs or on its own copy and MMA pipeline (grid barriers of the
+ *   forward chain, mbarriers).  A wait that reaches the limit abandons the call: its CTA sets the
+ *   plan's status word (sht_plan_check then returns SHT_ERR_TIMEOUT), the other CTAs leave at their
+ *   next wait, each waits up to one second for its own copies and MMAs in flight and releases its
+ *   tensor memory; the results of that call are invalid, later calls are unaffected.  Default 1.
+ */
+sht_status sht_plan_set_wait_limit(sht_plan_t plan, double seconds);
+
+/*
  * sht_plan_check - wait for the plan's queued work (synchronises the device) and report whether a
  *   bounded wait inside a tensor-core kernel gave up since the last check (SHT_ERR_TIMEOUT; the
  *   results of the affected call are then invalid).  Clears the flag.

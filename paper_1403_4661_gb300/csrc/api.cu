@@ -270,7 +270,8 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         Span sp(p, SHT_STAGE_SOLVE, s);
         const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off, p->d_tmaps};
         if (e == cudaSuccess)
-            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.bar, p->d_status, nsl, p->chain_grid, s);
+            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.bar, p->d_status, nsl, p->chain_grid,
+                                 p->wait_ns, s);
         p->launches += 1;
         return e;
     }
@@ -309,7 +310,8 @@ cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, do
         if (p->dtype != SHT_F64) {
             e = tc_slice_orders(w.a, L, batch, p->d_ptk_off, w.xS, w.xE, s);
             if (e == cudaSuccess)
-                e = tc_synthesis_all_orders(L, batch, p->ptE, p->d_tmaps, w.xE, w.tmX, w.g, p->d_status, s);
+                e = tc_synthesis_all_orders(L, batch, p->ptE, p->d_tmaps, w.xE, w.tmX, w.g, p->d_status,
+                                            p->wait_ns, s);
             p->launches += 1;
         } else {
             e = synthesis_all_orders(L, batch, p->pt, w.a, w.g, s);
@@ -526,6 +528,15 @@ sht_status sht_get_info(sht_plan_t p, sht_info *out) {
     out->kernel_launches = p->launches;
     out->refine_iterations = p->refine_iters;
     out->refine_last_update = p->refine_last;
+    return SHT_OK;
+}
+
+sht_status sht_plan_set_wait_limit(sht_plan_t p, double seconds) {
+    sht_status st = check_plan(p);
+    if (st != SHT_OK) return st;
+    if (!(seconds >= 1e-9 && seconds <= 60.0))
+        return set_error(SHT_ERR_INVALID_ARG, "wait limit must be in [1e-9, 60] seconds");
+    p->wait_ns = (uint64_t)(seconds * 1e9);
     return SHT_OK;
 }
 

@@ -53,6 +53,7 @@ struct ChainArgs {
                                      // lines
     int *eW, *eF;                    // [2][Nc] largest exponent fields of the columns of g_m, F_m
                                      // (slot m & 1); all of bar, eW, eF zeroed per launch
+    uint64_t wait_ns;                // limit of every wait on other CTAs or on the pipeline
     const unsigned char *tmaps;      // TMA maps of the table slices: order m at 2m (P_m^{-1}) and
                                      // 2m + 1 (P~ block), kTensorMapBytes each
     int *status;
@@ -112,7 +113,7 @@ __device__ bool grid_barrier(const ChainArgs &p, int *s_flag) {
             const uint64_t t0 = global_ns();
             while (*gen == g) {
                 if (aborted(p)) { ok = 0; break; }
-                if (global_ns() - t0 > 1000000000ull) { raise_abort(p, 2); ok = 0; break; }
+                if (global_ns() - t0 > p.wait_ns) { raise_abort(p, 2); ok = 0; break; }
                 __nanosleep(32);
             }
         }
@@ -216,7 +217,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             // stage st holds k-block kb once its TMA load has landed: issue its MMAs, then stage the
             // next block while they run
             {
-                const bool w = mbar_wait(smem_u32(&full[st]), (fills[st] - 1) & 1u);
+                const bool w = mbar_wait(smem_u32(&full[st]), (fills[st] - 1) & 1u, p.wait_ns);
                 if (!__syncthreads_and(w)) { ok = false; break; }
             }
             if (tid == 0) {
@@ -244,7 +245,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                 // the MMAs of k-block kb - 1 read stage ns: wait for them before refilling it;
                 // the vote keeps every thread on the same path if the wait gives up
                 const int ns = st ^ 1;
-                const bool w = uses[ns] == 0 || mbar_wait(smem_u32(&mbar[ns]), (uses[ns] - 1) & 1u);
+                const bool w = uses[ns] == 0 || mbar_wait(smem_u32(&mbar[ns]), (uses[ns] - 1) & 1u, p.wait_ns);
                 if (!__syncthreads_and(w)) { ok = false; break; }
                 load(kb + 1, ns);
                 fence_proxy_async();
@@ -253,7 +254,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             const int kdone = (kb + 1) * KB;
             if ((EXACT && kdone % CHUNK == 0) || kb == nkb - 1) {
                 // the commit of this stage covers every MMA issued so far
-                const bool w = mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u);
+                const bool w = mbar_wait(smem_u32(&mbar[st]), (uses[st] - 1) & 1u, p.wait_ns);
                 if (!__syncthreads_and(w)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t lane_base = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * kCols);
@@ -515,14 +516,14 @@ cudaError_t tc_prepare_chain(int *grid) {
 
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
                              double2 *coeffs, double *part, unsigned *words, int *status, int nsl,
-                             int grid, cudaStream_t s) {
+                             int grid, uint64_t wait_ns, cudaStream_t s) {
     ChainArgs p{};
     p.L = L; p.Nc = (int)(4 * batch);
     p.W = W; p.F = F; p.coeffs = coeffs;
     p.piS = t.piS; p.piE = t.piE; p.pik_off = t.pik_off;
     p.ptS = t.ptS; p.ptE = t.ptE; p.ptk_off = t.ptk_off;
     p.tmaps = t.tmaps;
-    p.part = part; p.bar = words; p.status = status;
+    p.part = part; p.bar = words; p.status = status; p.wait_ns = wait_ns;
     p.eW = reinterpret_cast<int *>(words + kChainBarWords);
     p.eF = p.eW + 2 * p.Nc;
     cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * tc_chain_words(batch), s);

@@ -111,7 +111,8 @@ struct sht_plan_s {
     int *d_status = nullptr;
 
     // refinement (SHT_BF16_REFINED, SHT_BF16X2_REFINED)
-    int chain_grid = 0;           // CTAs of the persistent order-chain kernel (tensor plans)
+    int chain_grid = 0;
+    uint64_t wait_ns = 1000000000ull;   // limit of the tensor kernels' waits (sht_plan_set_wait_limit)           // CTAs of the persistent order-chain kernel (tensor plans)
     int refine_nsl = 0;           // slices of the low-precision forward; 0: no refinement
     int refine_max_iters = 10;
     double refine_tol = 1e-11;
@@ -199,7 +200,6 @@ cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, doub
 constexpr int kTcSlices = 8;     // slices per operand
 constexpr int kTcSliceBits = 7;  // bits per slice
 cudaError_t tc_prepare_kernels();
-constexpr int kNumSMs = 152;
 // Plan tables: slices of every order's P~ block (inverses = false; slice block m at
 // kTcSlices * L * koff[m] elements, exponents at m * L) or P_m^{-1} block (inverses = true; slices
 // at kTcSlices * koff[m], exponents at rows_off(L, m)).
@@ -227,7 +227,7 @@ constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 
 cudaError_t tc_prepare_chain(int *grid);
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
                              double2 *coeffs, double *part, unsigned *words, int *status, int nsl,
-                             int grid, cudaStream_t s);
+                             int grid, uint64_t wait_ns, cudaStream_t s);
 // Device words the chain kernel needs beside W, F and part (barrier, column scales).
 int64_t tc_chain_words(int64_t batch);
 // TMA maps of the per-call X slices (order m at m: {kp, 4B, S}, boxes 32 x 64 x S), written to a
@@ -237,7 +237,7 @@ cudaError_t tc_x_tensor_maps(int L, int64_t batch, const __nv_bfloat16 *xS,
 // Eq. (11) for every order in one launch: Gt[m] (L x 4B) = P~_m X_m.
 cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const int *ptE, const unsigned char *tmA,
                                     const int *xE, const unsigned char *tmB, double *Gt, int *status,
-                                    cudaStream_t s);
+                                    uint64_t wait_ns, cudaStream_t s);
 
 // planner.cu: greedy condition-number ordering (indices into the equiangular set)
 sht_status greedy_order(int L, std::vector<int> &order);

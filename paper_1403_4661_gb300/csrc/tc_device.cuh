@@ -49,12 +49,14 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Waits for phase `parity` of the barrier; false after about one second.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// Waits for phase `parity` of the barrier; false once `limit_ns` have passed (default: the one
+// second used for the waits on a CTA's own copies and MMAs before it releases its memory).
+constexpr uint64_t kOwnWaitNs = 1000000000ull;
+__device__ bool mbar_wait(uint32_t a, uint32_t parity, uint64_t limit_ns = kOwnWaitNs) {
     if (mbar_try_wait(a, parity)) return true;
     const uint64_t t0 = global_ns();
     while (!mbar_try_wait(a, parity))
-        if (global_ns() - t0 > 1000000000ull) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }

@@ -126,6 +126,7 @@ struct SynArgs {
     const unsigned char *tmA, *tmB;        // TMA maps: P~ block of order m at (2m + 1), X slices at m
     double *Gt;                            // order-major G: m * L * Nc
     int *status;
+    uint64_t wait_ns;                      // limit of the pipeline waits
 };
 
 constexpr int kSynThreads = 256;
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_synthesis(SynArgs p) {
         const int st = kb & 1;
         const uint32_t par = (uint32_t)(kb >> 1) & 1u;   // use kb >> 1 of stage st
         if (tid == 0 && ok0) {
-            ok0 = mbar_wait(smem_u32(&full[st]), par);
+            ok0 = mbar_wait(smem_u32(&full[st]), par, p.wait_ns);
             if (ok0) {
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
@@ -200,14 +201,14 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_synthesis(SynArgs p) {
                 ++commits;
                 // refill the other stage once the MMAs of block kb - 1 (its last reader) are done
                 if (kb + 1 < nkb) {
-                    if (kb >= 1) ok0 = mbar_wait(smem_u32(&mbar[st ^ 1]), (uint32_t)((kb - 1) >> 1) & 1u);
+                    if (kb >= 1) ok0 = mbar_wait(smem_u32(&mbar[st ^ 1]), (uint32_t)((kb - 1) >> 1) & 1u, p.wait_ns);
                     if (ok0) { load(kb + 1); ++loads; }
                 }
             }
         }
         if (((kb + 1) * KB) % CHUNK == 0 || kb == nkb - 1) {
             // the commit of block kb covers every MMA issued so far
-            const bool w = mbar_wait(smem_u32(&mbar[st]), par);
+            const bool w = mbar_wait(smem_u32(&mbar[st]), par, p.wait_ns);
             alive = __syncthreads_and(w && (tid != 0 || ok0));
             if (!alive) break;
             tc_fence_after();
@@ -302,8 +303,9 @@ cudaError_t tc_x_tensor_maps(int L, int64_t batch, const __nv_bfloat16 *xS,
 
 cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const int *ptE, const unsigned char *tmA,
                                     const int *xE, const unsigned char *tmB, double *Gt, int *status,
-                                    cudaStream_t s) {
+                                    uint64_t wait_ns, cudaStream_t s) {
     SynArgs p{};
+    p.wait_ns = wait_ns;
     p.L = L; p.Nc = (int)(4 * batch); p.ptE = ptE; p.xE = xE; p.tmA = tmA; p.tmB = tmB; p.Gt = Gt;
     p.status = status;
     const int64_t grid = (int64_t)L * cdiv(L, MT) * cdiv(p.Nc, NT);

@@ -34,7 +34,7 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
             "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement",
-            "sht_forward_uneven", "sht_inverse_uneven"]
+            "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit"]
 STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
 
 
@@ -82,6 +82,7 @@ def load_library(path=LIB_PATH):
     lib.sht_status_string.restype = ctypes.c_char_p
     lib.sht_plan_check.argtypes = [P]
     lib.sht_plan_set_refinement.argtypes = [P, ctypes.c_int, ctypes.c_double]
+    lib.sht_plan_set_wait_limit.argtypes = [P, ctypes.c_double]
     for name in ("sht_forward_uneven", "sht_inverse_uneven"):
         getattr(lib, name).argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i64), P, P, P]
@@ -297,6 +298,10 @@ class Plan:
     def set_refinement(self, max_iters=10, tol=1e-11):
         """Iteration control of refined plans (tol = 0: fixed iterations, no synchronisation)."""
         sht_plan_set_refinement(self.handle, max_iters, tol)
+
+    def set_wait_limit(self, seconds=1.0):
+        """Limit of the tensor kernels' waits on other CTAs and on their pipeline."""
+        _check(load_library().sht_plan_set_wait_limit(self.handle, float(seconds)))
 
     def check(self):
         """Synchronise and raise if a bounded device wait gave up since the last check."""

@@ -10,7 +10,7 @@ import torch
 
 from oracle import sht as osht
 from paper_1403_4661_gb300 import synth
-from tests.helpers import oracle_thetas, tol_samples
+from tests.helpers import oracle_order, oracle_thetas, tol_samples
 
 pytestmark = pytest.mark.gpu
 
@@ -74,6 +74,17 @@ def test_library_greedy_ordering_matches_oracle(L):
     from paper_1403_4661_gb300.sht import Plan
     p = Plan(L)  # library planner on the GPU
     np.testing.assert_allclose(p.theta, oracle_thetas(L), rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("L", [512, 1024])
+def test_library_greedy_ordering_matches_stored_oracle_orderings(L):
+    """The GPU planner at the bench's sizes against the oracle's stored orderings (index work:
+    exact)."""
+    from paper_1403_4661_gb300.sht import Plan
+    p = Plan(L, dtype="f64")
+    t = np.rint((np.asarray(p.theta) * (2 * L - 1) / np.pi - 1.0) / 2.0).astype(np.int64)
+    ref = oracle_order(L)
+    assert np.array_equal(t, ref), f"{int(np.sum(t != ref))} of {L} rings differ"
 
 
 @pytest.mark.parametrize("L,B", [(512, 256), (1024, 64)])

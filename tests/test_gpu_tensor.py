@@ -131,3 +131,25 @@ def test_tensor_deterministic_and_graph_capture():
         assert torch.equal(c2, ref)
     p.check()
     assert (ref - c).abs().max().item() <= 1e-11
+
+
+def test_wait_limit_timeout_is_reported_and_the_plan_recovers():
+    """A wait limit of 1 ns makes the tensor kernels' waits (grid barriers, mbarriers) give up at
+    once: the call is abandoned with SHT_ERR_TIMEOUT in the status word, the context stays usable
+    and the next call at the default limit gives the normal result."""
+    from paper_1403_4661_gb300.sht import SHTError
+    L, B = 96, 4
+    p = _plan(L)
+    s = _gpu(synth.uniform_samples(L, B, 3))
+    ref = p.forward(s)
+    p.check()
+    with pytest.raises(SHTError):
+        p.set_wait_limit(0.0)
+    p.set_wait_limit(1e-9)
+    p.forward(s)
+    p.inverse(ref)
+    with pytest.raises(SHTError, match="TIMEOUT"):
+        p.check()
+    p.set_wait_limit(1.0)
+    assert torch.equal(p.forward(s), ref)
+    p.check()
