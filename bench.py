@@ -111,13 +111,31 @@ class ClockSampler:
 
 
 def _dist():
+    """(dist, rank, world size, local rank) from the torchrun environment; NCCL on GPUs, gloo
+    without (the CPU tests of the multi-rank logic)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
+        import torch
         import torch.distributed as dist
         if not dist.is_initialized():
-            dist.init_process_group("nccl")
+            dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
     return None, 0, 1, 0
+
+
+def _max_over_ranks(value, dist, device="cpu"):
+    """The slowest rank's figure (a step is done when every rank is done)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def _whole_job_rate(world_size, batch_per_rank, ms_per_step):
+    """Signals per second of the whole job: every rank transforms its own batch (weak scaling)."""
+    return world_size * batch_per_rank / (ms_per_step * 1e-3)
 
 
 def _oracle_sample(L, seed, frac):
@@ -285,10 +303,7 @@ def run_ours(args):
         launches = captured_launches * args.steps
         stages = plan.stage_times()
         stage_steps = 1
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = _max_over_ranks(ms, dist, dev)
 
     # ---- end to end: host buffers, copies inside the timed region ----------------------------
     out_host = torch.empty_like(c_host).pin_memory()
@@ -309,10 +324,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = t.item()
+    ms_e2e = _max_over_ranks(ms_e2e, dist, dev)
     err_e2e = float(np.abs(out_host.numpy() - c_host.numpy()).max())
 
     if rank != 0:
@@ -360,7 +372,7 @@ def run_ours(args):
                 "traffic": _traffic_record("synthesis_f64", L, B)}
     roof["stage_ms_per_step"] = {k: v[0] / stage_steps for k, v in stages.items()}
     roof["stage_launch_spans_per_step"] = {k: v[1] / stage_steps for k, v in stages.items()}
-    value = ws * B / (ms * 1e-3)
+    value = _whole_job_rate(ws, B, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -372,7 +384,7 @@ def run_ours(args):
         "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": ws * B / (ms_e2e * 1e-3), "unit": "signals/s",
+        "e2e": {"value": _whole_job_rate(ws, B, ms_e2e), "unit": "signals/s",
                 "h2d_bytes_per_step": 16 * L * L * B, "d2h_bytes_per_step": 16 * L * L * B},
         "clocks": clk,
         "gpu_launches": launches,

@@ -48,9 +48,10 @@ struct ChainArgs {
     double2 *coeffs;
     const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // P_m^{-1} slices
     const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;   // P~ slices
-    double *part;                    // K-split partials: splits x M x Nc
-    unsigned *bar;                   // [0] arrivals, [32] generation, [64] abort: separate 128-byte
-                                     // lines
+    long long *part;                 // K-split partials, int64 at the scale of the output element
+                                     // (2^-(eA + eB) 2^shift): splits x M x Nc
+    unsigned *bar;                   // [0] arrivals (monotonic within a launch), [64] abort:
+                                     // separate 128-byte lines
     int *eW, *eF;                    // [2][Nc] largest exponent fields of the columns of g_m, F_m
                                      // (slot m & 1); all of bar, eW, eF zeroed per launch
     uint64_t wait_ns;                // limit of every wait on other CTAs or on the pipeline
@@ -97,24 +98,22 @@ __device__ __forceinline__ void raise_abort(const ChainArgs &p, int bit) {
     atomicExch(p.bar + 64, 1u);
 }
 
-// Grid-wide barrier; false (for every thread of the CTA) once any CTA has given up.
-__device__ bool grid_barrier(const ChainArgs &p, int *s_flag) {
+// Grid-wide barrier; false (for every thread of the CTA) once any CTA has given up.  The arrival
+// counter only grows during a launch: barrier i is passed when it reaches i * G, so there is no
+// reset and no second word to publish.
+__device__ bool grid_barrier(const ChainArgs &p, int *s_flag, unsigned &target) {
     __syncthreads();
+    target += gridDim.x;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned *gen = p.bar + 32;
-        const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(p.bar, 1u) == gridDim.x - 1) {
-            atomicExch(p.bar, 0u);
-            __threadfence();
-            atomicAdd(p.bar + 32, 1u);
-        } else {
+        atomicAdd(p.bar, 1u);
+        volatile unsigned *cnt = p.bar;
+        if (*cnt < target) {
             const uint64_t t0 = global_ns();
-            while (*gen == g) {
+            while (*cnt < target) {
                 if (aborted(p)) { ok = 0; break; }
                 if (global_ns() - t0 > p.wait_ns) { raise_abort(p, 2); ok = 0; break; }
-                __nanosleep(32);
             }
         }
         __threadfence();
@@ -126,11 +125,10 @@ __device__ bool grid_barrier(const ChainArgs &p, int *s_flag) {
 }
 
 // Largest exponent field of each column over `rows` rows of the row-major block X (Nc columns)
-// into ef[Nc] (atomicMax).  A quarter of the CTAs take rows c, c + G/4, ..; each thread keeps the
-// maximum of its column over eight rows in flight at a time, so each column sees G/4 atomics.
+// into ef[Nc] (atomicMax).  CTA c takes rows c, c + G, ..; each thread keeps the maximum of its
+// column over eight rows in flight at a time, so each column sees at most G atomics.
 __device__ void column_fields(const ChainArgs &p, const double *X, int rows, int *ef) {
-    const int Nc = p.Nc, C = max(1, (int)gridDim.x / 4);
-    if ((int)blockIdx.x >= C) return;
+    const int Nc = p.Nc, C = (int)gridDim.x;
     for (int j = threadIdx.x; j < Nc; j += kThreads) {
         int mf = 0;
         for (int r0 = blockIdx.x; r0 < rows; r0 += 8 * C) {
@@ -155,7 +153,6 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                                        uint32_t uses[2], uint32_t fills[2], bool &ok) {
     constexpr bool EXACT = NSL == S;
     constexpr int NREG = EXACT ? REGIONS : 1;
-    constexpr int SHIFT = EXACT ? ACC_SHIFT : 40;
     const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
     const int Nc = p.Nc, M = jb.M;
     const int items = jb.tiles * jb.splits;
@@ -294,47 +291,53 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
 
         const int row = row0 + (warp & 3) * 32 + (tid & 31);
         if (row < M) {
-            const int er = jb.eA[row];
 #pragma unroll
             for (int g = 0; g < kCols / 4; ++g) {
                 const int cl = half * kCols + 4 * g, c0 = col0 + cl;
                 if (c0 >= Nc) break;
-                double v[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = i64_scaled(acc[4 * g + q], er + s_eb[cl + q] - SHIFT);
-                double *pp = p.part + ((int64_t)y * M + row) * Nc + c0;
-                *reinterpret_cast<double2 *>(pp) = make_double2(v[0], v[1]);
-                *reinterpret_cast<double2 *>(pp + 2) = make_double2(v[2], v[3]);
-                asm volatile("" ::: "memory");   // one group at a time (register pressure)
+                long long *pp = p.part + ((int64_t)y * M + row) * Nc + c0;
+                *reinterpret_cast<longlong2 *>(pp) = make_longlong2(acc[4 * g], acc[4 * g + 1]);
+                *reinterpret_cast<longlong2 *>(pp + 2) = make_longlong2(acc[4 * g + 2], acc[4 * g + 3]);
             }
         }
     }
 }
 
-// Sum of the K-split partials of row r, columns c0..c0+3, in split order (deterministic).
-__device__ __forceinline__ void sum_partials(const ChainArgs &p, int M, int splits, int r, int c0, double v[4]) {
+// Exact int64 sum of the K-split partials of row r, columns c0..c0+3 (all at the scale of the
+// output element), then one conversion: 2^(eA_r + eB_c - shift) * sum.
+struct Scales {
+    const int *eA;     // row scale exponents
+    const int *fB;     // exponent fields of the right-hand side's columns
+    int shift;
+};
+__device__ __forceinline__ void sum_partials(const ChainArgs &p, const Scales &sc, int M, int splits, int r,
+                                             int c0, double v[4]) {
     const int Nc = p.Nc;
-    v[0] = v[1] = v[2] = v[3] = 0.0;
+    long long t[4] = {0, 0, 0, 0};
     for (int y0 = 0; y0 < splits; y0 += 8) {
-        double2 a[8], b[8];
+        longlong2 a[8], b[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u)
             if (y0 + u < splits) {
-                const double2 *pp = reinterpret_cast<const double2 *>(p.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
+                const longlong2 *pp = reinterpret_cast<const longlong2 *>(p.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
                 a[u] = __ldcg(pp);
                 b[u] = __ldcg(pp + 1);
             }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (y0 + u < splits) { v[0] += a[u].x; v[1] += a[u].y; v[2] += b[u].x; v[3] += b[u].y; }
+            if (y0 + u < splits) { t[0] += a[u].x; t[1] += a[u].y; t[2] += b[u].x; t[3] += b[u].y; }
     }
+    const int er = sc.eA[r] - sc.shift;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = i64_scaled(t[q], er + scale_from_field(__ldcg(sc.fB + c0 + q)));
 }
 
 // Solve epilogue: F_m rows and f_l^{+-m}; largest exponent fields of F_m's columns into ef.
 // When the grid's thread count is a multiple of the column groups, every thread of a CTA stays on
 // one group and the CTA's groups are a window of kThreads groups: the maxima are first gathered in
 // shared memory, one global atomicMax per CTA and column.
-__device__ __noinline__ void reduce_solve(const ChainArgs &p, const EpiArgs &epi, int M, int splits, int *ef) {
+__device__ __noinline__ void reduce_solve(const ChainArgs &p, const EpiArgs &epi, const Scales &sc, int M,
+                                          int splits, int *ef) {
     const int groups = p.Nc / 4;
     const int64_t total = (int64_t)M * groups, T = (int64_t)gridDim.x * kThreads;
     __shared__ int s_ef[4 * kThreads];
@@ -346,7 +349,7 @@ __device__ __noinline__ void reduce_solve(const ChainArgs &p, const EpiArgs &epi
     for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
         const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
         double v[4];
-        sum_partials(p, M, splits, r, 4 * g, v);
+        sum_partials(p, sc, M, splits, r, 4 * g, v);
         epilogue_row4<EPI_SOLVE>(epi, r, 4 * g, v);
         const int w = g - g0 < 0 ? g - g0 + groups : g - g0;   // position in the CTA's window
 #pragma unroll
@@ -368,14 +371,15 @@ __device__ __noinline__ void reduce_solve(const ChainArgs &p, const EpiArgs &epi
 // Alias epilogue: subtract from the bins of rings k < m; then the rows of g_{m-1} are final:
 // ring m - 1 (row 0 of block m - 1, just updated here by the thread that wrote it) and rings
 // m .. L-1 (rows 1 ..), whose largest exponent fields go to ef.
-__device__ __noinline__ void reduce_alias(const ChainArgs &p, const EpiArgs &epi, int m, int splits, int *ef) {
+__device__ __noinline__ void reduce_alias(const ChainArgs &p, const EpiArgs &epi, const Scales &sc, int m,
+                                          int splits, int *ef) {
     const int L = p.L, Nc = p.Nc, groups = Nc / 4;
     const int64_t total = (int64_t)m * groups, T = (int64_t)gridDim.x * kThreads;
     const double *g1 = p.W + rows_off(L, m - 1) * Nc;   // block m - 1
     for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
         const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
         double v[4];
-        sum_partials(p, m, splits, r, 4 * g, v);
+        sum_partials(p, sc, m, splits, r, 4 * g, v);
         epilogue_row4<EPI_ALIAS>(epi, r, 4 * g, v);
         if (r == m - 1)
 #pragma unroll
@@ -410,11 +414,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     const uint32_t tbase = tmem_slot;
 
     uint32_t uses[2] = {0u, 0u}, fills[2] = {0u, 0u};
+    unsigned target = 0;   // arrivals that complete the next grid barrier
     bool ok = true, mma_ok = true;
     const int L = p.L, Nc = p.Nc;
     // column scales of g_{L-1}: the single ring L-1
     column_fields(p, p.W + rows_off(L, L - 1) * Nc, 1, p.eW + ((L - 1) & 1) * Nc);
-    ok = grid_barrier(p, &s_flag);
+    ok = grid_barrier(p, &s_flag, target);
     for (int m = L - 1; m >= 0 && ok; --m) {
         const int n = L - m, kp = (n + 7) & ~7, sl = m & 1;
         // slots of order m - 1: no reader until after the next barrier (last read by order m + 1)
@@ -427,20 +432,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
                                 p.W + rows_off(L, m) * Nc, p.eW + sl * Nc, n, n, Nc);
         mma_phase<NSL>(p, js, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
-        if (!(ok = grid_barrier(p, &s_flag))) break;
+        if (!(ok = grid_barrier(p, &s_flag, target))) break;
         const EpiArgs es{p.F + rows_off(L, m) * Nc, Nc, nullptr, m, L, Nc, p.coeffs, nullptr};
-        reduce_solve(p, es, n, js.splits, p.eF + sl * Nc);
-        if (!(ok = grid_barrier(p, &s_flag))) break;
+        const Scales ss{js.eA, js.eB, NSL == S ? ACC_SHIFT : 40};
+        reduce_solve(p, es, ss, n, js.splits, p.eF + sl * Nc);
+        if (!(ok = grid_barrier(p, &s_flag, target))) break;
         if (m == 0) break;
         // Eqs. (15)-(16): orders +-m out of the bins of rings k < m
         const Job ja = make_job(p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes, p.ptE + (int64_t)m * L, kp,
                                 p.F + rows_off(L, m) * Nc, p.eF + sl * Nc, m, n, Nc);
         mma_phase<NSL>(p, ja, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
-        if (!(ok = grid_barrier(p, &s_flag))) break;
+        if (!(ok = grid_barrier(p, &s_flag, target))) break;
         const EpiArgs ea{nullptr, Nc, nullptr, m, L, Nc, nullptr, p.W};
-        reduce_alias(p, ea, m, ja.splits, p.eW + (sl ^ 1) * Nc);
-        if (!(ok = grid_barrier(p, &s_flag))) break;
+        const Scales sa{ja.eA, ja.eB, NSL == S ? ACC_SHIFT : 40};
+        reduce_alias(p, ea, sa, m, ja.splits, p.eW + (sl ^ 1) * Nc);
+        if (!(ok = grid_barrier(p, &s_flag, target))) break;
     }
     if (!mma_ok) {
         // let the TMA loads and MMAs in flight finish (bounded) before the CTA releases its
@@ -523,7 +530,7 @@ cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double 
     p.piS = t.piS; p.piE = t.piE; p.pik_off = t.pik_off;
     p.ptS = t.ptS; p.ptE = t.ptE; p.ptk_off = t.ptk_off;
     p.tmaps = t.tmaps;
-    p.part = part; p.bar = words; p.status = status; p.wait_ns = wait_ns;
+    p.part = reinterpret_cast<long long *>(part); p.bar = words; p.status = status; p.wait_ns = wait_ns;
     p.eW = reinterpret_cast<int *>(words + kChainBarWords);
     p.eF = p.eW + 2 * p.Nc;
     cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * tc_chain_words(batch), s);
