@@ -27,8 +27,12 @@ __device__ __forceinline__ double2 conjd(double2 a) { return make_double2(a.x, -
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 
-// In-place radix-2 decimation-in-time FFT of a[0..M) in shared memory; natural-order input and
-// output.  tw[t] = e^{-2 pi i t / Mmax}; inverse = conjugate twiddles, unnormalised.
+// In-place decimation-in-time FFT of a[0..M) in shared memory, natural-order input and output:
+// bit-reversal permutation, then the radix-2 stages taken two at a time as radix-4 butterflies
+// (stages s, s+1 with half-width h share the twiddle u = W_{4h}^j: the four outputs need u x2,
+// u^2 x1, u^3 x3 and the factor W_{4h}^h = -i, i.e. 3 complex products instead of 4), plus one
+// radix-2 stage of twiddle 1 when log2 M is odd.  tw[t] = e^{-2 pi i t / Mmax}, t < Mmax;
+// inverse = conjugate twiddles, unnormalised.
 __device__ void block_fft(double2 *a, int M, int logM, const double2 *__restrict__ tw, int Mmax,
                           bool inverse) {
     for (int i = threadIdx.x; i < M; i += blockDim.x) {
@@ -36,18 +40,41 @@ __device__ void block_fft(double2 *a, int M, int logM, const double2 *__restrict
         if (i < j) { double2 t = a[i]; a[i] = a[j]; a[j] = t; }
     }
     __syncthreads();
-    for (int s = 1; s <= logM; ++s) {
-        const int half = 1 << (s - 1);
-        const int stride = Mmax >> s;
+    int s = 1;
+    if (logM & 1) {
         for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-            const int pos = t & (half - 1);
-            const int i = ((t >> (s - 1)) << s) + pos;
-            const int j = i + half;
-            double2 w = __ldg(&tw[pos * stride]);
-            if (inverse) w.y = -w.y;
-            double2 u = a[i], v = cmul(a[j], w);
-            a[i] = cadd(u, v);
-            a[j] = csub(u, v);
+            const double2 u = a[2 * t], v = a[2 * t + 1];
+            a[2 * t] = cadd(u, v);
+            a[2 * t + 1] = csub(u, v);
+        }
+        __syncthreads();
+        s = 2;
+    }
+    for (; s < logM; s += 2) {
+        const int h = 1 << (s - 1);
+        const int stride = Mmax >> (s + 1);   // u = W_{4h}^j = tw[j * stride]
+        for (int t = threadIdx.x; t < (M >> 2); t += blockDim.x) {
+            const int j = t & (h - 1);
+            const int i0 = ((t >> (s - 1)) << (s + 1)) + j;
+            const double2 x0 = a[i0], x1 = a[i0 + h], x2 = a[i0 + 2 * h], x3 = a[i0 + 3 * h];
+            double2 t1 = x1, t2 = x2, t3 = x3;
+            if (h > 1) {   // h == 1: j == 0, every twiddle is 1
+                double2 u = __ldg(&tw[j * stride]), u2 = __ldg(&tw[2 * j * stride]), u3 = __ldg(&tw[3 * j * stride]);
+                if (inverse) { u.y = -u.y; u2.y = -u2.y; u3.y = -u3.y; }
+                t1 = cmul(x1, u2);
+                t2 = cmul(x2, u);
+                t3 = cmul(x3, u3);
+            }
+            const double2 A = cadd(x0, t1), Bm = csub(x0, t1), C = cadd(t2, t3), D = csub(t2, t3);
+            a[i0] = cadd(A, C);
+            a[i0 + 2 * h] = csub(A, C);
+            if (!inverse) {   // W_{4h}^h = -i
+                a[i0 + h] = make_double2(Bm.x + D.y, Bm.y - D.x);
+                a[i0 + 3 * h] = make_double2(Bm.x - D.y, Bm.y + D.x);
+            } else {          // +i
+                a[i0 + h] = make_double2(Bm.x - D.y, Bm.y + D.x);
+                a[i0 + 3 * h] = make_double2(Bm.x + D.y, Bm.y - D.x);
+            }
         }
         __syncthreads();
     }
@@ -55,7 +82,7 @@ __device__ void block_fft(double2 *a, int M, int logM, const double2 *__restrict
 
 __global__ void k_twiddle(double2 *tw, int Mmax) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= Mmax / 2) return;
+    if (t >= Mmax) return;
     double s, c;
     sincospi(2.0 * (double)t / (double)Mmax, &s, &c);
     tw[t] = make_double2(c, -s);
@@ -303,7 +330,7 @@ cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s)
         total += M;
     }
     cudaError_t e;
-    size_t b_tw = sizeof(double2) * (Mmax / 2), b_ch = sizeof(double2) * (size_t)L * L;
+    size_t b_tw = sizeof(double2) * Mmax, b_ch = sizeof(double2) * (size_t)L * L;
     size_t b_f = sizeof(double2) * (size_t)(total > 0 ? total : 1);
     if ((e = cudaMalloc(&dp.twiddle, b_tw)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&dp.chirp, b_ch)) != cudaSuccess) return e;
@@ -313,7 +340,7 @@ cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s)
     bytes = b_tw + b_ch + b_f + sizeof(int64_t) * L + sizeof(int) * L;
     cudaMemcpyAsync(dp.filt_off, dp.h_filt_off.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(dp.filt_M, dp.h_filt_M.data(), sizeof(int) * L, cudaMemcpyHostToDevice, s);
-    k_twiddle<<<(Mmax / 2 + 255) / 256, 256, 0, s>>>(dp.twiddle, Mmax);
+    k_twiddle<<<(Mmax + 255) / 256, 256, 0, s>>>(dp.twiddle, Mmax);
     int64_t LL = (int64_t)L * L;
     k_chirp<<<(unsigned)((LL + 255) / 256), 256, 0, s>>>(dp.chirp, L);
     if ((e = set_ring_kernel_limits(Mmax)) != cudaSuccess) return e;

@@ -63,7 +63,7 @@ struct DftPlan {
     double2 *filt = nullptr;       // per Bluestein ring: FFT_M of the conjugate chirp, scaled
     int64_t *filt_off = nullptr;   // device, per ring (-1 for direct rings)
     int *filt_M = nullptr;         // device, per ring convolution length (0 for direct rings)
-    double2 *twiddle = nullptr;    // e^{-2 pi i t / Mmax}, t < Mmax / 2
+    double2 *twiddle = nullptr;    // e^{-2 pi i t / Mmax}, t < Mmax
     std::vector<int64_t> h_filt_off;
     std::vector<int> h_filt_M;
 };
