@@ -36,7 +36,7 @@ constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring k
 void free_ws(Workspace &w) {
     cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
     cudaFree(w.xS); cudaFree(w.xE); cudaFree(w.tmX);
-    cudaFree(w.r); cudaFree(w.dx); cudaFree(w.bar);
+    cudaFree(w.r); cudaFree(w.dx); cudaFree(w.bar); cudaFree(w.part2);
     w = Workspace{};
 }
 
@@ -85,8 +85,9 @@ sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
         e = cudaMalloc(&w.xS, xs);
         if (e == cudaSuccess) e = cudaMalloc(&w.xE, sizeof(int) * Nc * L);
         if (e == cudaSuccess) e = cudaMalloc(&w.bar, words);
+        if (e == cudaSuccess) e = cudaMalloc(&w.part2, sp);
         if (e == cudaSuccess) e = tc_x_tensor_maps(p->L, batch, w.xS, p->ptk_off, &w.tmX);
-        bytes += xs + sizeof(int) * Nc * L + words + (uint64_t)p->L * kTensorMapBytes;
+        bytes += xs + sizeof(int) * Nc * L + words + sp + (uint64_t)p->L * kTensorMapBytes;
     }
     if (e != cudaSuccess) {
         free_ws(w);
@@ -270,8 +271,8 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         Span sp(p, SHT_STAGE_SOLVE, s);
         const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off, p->d_tmaps};
         if (e == cudaSuccess)
-            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.bar, p->d_status, nsl, p->chain_grid,
-                                 p->wait_ns, s);
+            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.part2, w.bar, p->d_status, nsl,
+                                 p->chain_grid, p->wait_ns, s);
         p->launches += 1;
         return e;
     }

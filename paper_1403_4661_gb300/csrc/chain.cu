@@ -7,14 +7,16 @@
 // orders run strictly in sequence; per order the work is two small contractions, n x n and
 // m x n by n x 4B.  As separate launches each order costs several kernel starts, tensor-memory
 // allocations and mostly idle SMs; here one CTA per SM stays resident for the whole chain, keeps
-// its tensor memory and mbarriers, and the steps of an order are four phases separated by
+// its tensor memory and mbarriers, and the steps of an order are three phases separated by
 // grid-wide barriers:
 //     solve: tiles x K-splits of P_m^{-1} g_m (tcgen05 on exact BF16 slices)      | barrier
-//     sum of the K-split partials in split order -> F_m, f_l^{+-m};
-//         column scales of F_m (atomicMax of the exponent fields)                  | barrier
+//     sum of the solve's K-split partials -> F_m, f_l^{+-m}, column scales of F_m;
+//         order m+1's alias partials subtracted from the bins of rings k < m;
+//         column scales of g_{m-1} without its first row (rings >= m, final now)  | barrier
 //     alias: tiles x K-splits of P~_m(rings k < m) F_m                             | barrier
-//     sum of the partials, subtracted from the bins of rings k < m;
-//         column scales of g_{m-1} (its rows are final now)                        | barrier
+// Order m's alias products reach ring m - 1, the first row of g_{m-1}, before they are summed
+// into the bins: the items of solve m - 1 add that row's partials up themselves (a few hundred
+// values), so no phase waits for the alias subtraction, which runs beside the next reduction.
 // The right-hand sides are read in float64 and cut into slices while they are staged in shared
 // memory, with the column scales the previous phase gathered; the plan tables (P_m^{-1}, P~) are
 // pre-sliced.
@@ -48,22 +50,48 @@ struct ChainArgs {
     double2 *coeffs;
     const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // P_m^{-1} slices
     const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;   // P~ slices
-    long long *part;                 // K-split partials, int64 at the scale of the output element
-                                     // (2^-(eA + eB) 2^shift): splits x M x Nc
+    long long *part_s, *part_a;      // K-split partials of the solves and of the alias products,
+                                     // int64 at the scale of the output element (2^-(eA + eB)
+                                     // 2^shift): splits x M x Nc
     unsigned *bar;                   // [0] arrivals (monotonic within a launch), [64] abort:
                                      // separate 128-byte lines
-    int *eW, *eF;                    // [2][Nc] largest exponent fields of the columns of g_m, F_m
-                                     // (slot m & 1); all of bar, eW, eF zeroed per launch
+    int *eW, *eF;                    // [2][Nc] largest exponent fields of the columns of g_m
+                                     // without its first row, and of F_m (slot m & 1)
+    int *fS;                         // [Nc] fields of g_m's columns, first row included
+                                     // (all of bar, eW, eF, fS zeroed per launch)
     uint64_t wait_ns;                // limit of every wait on other CTAs or on the pipeline
     const unsigned char *tmaps;      // TMA maps of the table slices: order m at 2m (P_m^{-1}) and
                                      // 2m + 1 (P~ block), kTensorMapBytes each
     int *status;
 };
 
+// Exact int64 sum of K-split partials, then one conversion: 2^(eA_r + eB_c - shift) * sum.
+struct Scales {
+    const int *eA;     // row scale exponents
+    const int *fB;     // exponent fields of the right-hand side's columns
+    int shift;
+};
+struct Partials {
+    const long long *part;
+    int M, splits;
+    Scales sc;
+};
+
+// First row of a solve's right-hand side g_m: ring m, whose bins +-m still hold order m+1's
+// alias contribution; `a` is the bin alias_m(m + 1) it was aliased into.
+struct FirstRow {
+    bool pending;      // m + 1 < L
+    Partials alias;    // order m+1's alias partials (row m of them is ring m)
+    int a;
+};
+
 // One contraction C (M x Nc) = A (M x K, plan slices) B (K x Nc, float64, row-major).
 struct Job {
     const void *tmap; const int *eA; int kp;   // A: TMA map {kp, rows, slices}, row scales
-    const double *B; const int *eB;  // eB: exponent fields of B's columns
+    const double *B; const int *eB;  // eB: exponent fields of B's columns (the solve: without the
+                                     // first row, which the items complete with `first`)
+    long long *part;                 // destination of the partials
+    const FirstRow *first;           // solves: completion of the first row (null: alias products)
     int M, K, tiles_n, tiles, splits, kchunk;
 };
 
@@ -73,6 +101,7 @@ __device__ Job make_job(const void *tmap, const int *eA, int kp, const double *B
                         int K, int Nc) {
     Job j;
     j.tmap = tmap; j.eA = eA; j.kp = kp; j.B = B; j.eB = eB; j.M = M; j.K = K;
+    j.part = nullptr; j.first = nullptr;
     j.tiles_n = cdiv_i(Nc, NT);
     j.tiles = cdiv_i(M, MT) * j.tiles_n;
     j.splits = 1;
@@ -145,6 +174,44 @@ __device__ void column_fields(const ChainArgs &p, const double *X, int rows, int
     }
 }
 
+// Exact int64 sum of the K-split partials of row r, columns c0..c0+3 (all at the scale of the
+// output element), then one conversion: 2^(eA_r + eB_c - shift) * sum.
+__device__ __forceinline__ void sum_partials(const ChainArgs &p, const Partials &pa, int r, int c0, double v[4]) {
+    const int Nc = p.Nc, M = pa.M, splits = pa.splits;
+    long long t[4] = {0, 0, 0, 0};
+    for (int y0 = 0; y0 < splits; y0 += 8) {
+        longlong2 a[8], b[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (y0 + u < splits) {
+                const longlong2 *pp = reinterpret_cast<const longlong2 *>(pa.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
+                a[u] = __ldcg(pp);
+                b[u] = __ldcg(pp + 1);
+            }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (y0 + u < splits) { t[0] += a[u].x; t[1] += a[u].y; t[2] += b[u].x; t[3] += b[u].y; }
+    }
+    const int er = pa.sc.eA[r] - pa.sc.shift;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = i64_scaled(t[q], er + scale_from_field(__ldcg(pa.sc.fB + c0 + q)));
+}
+
+// The alias subtraction from one bin group of a ring (signal b's 4 columns (+q re, +q im, -q re,
+// -q im) of the row that holds bin a): v = (G_{+m} re, im, G_{-m} re, im), as in EPI_ALIAS.
+__device__ __forceinline__ void alias_update(double w[4], int a, const double v[4]) {
+    if (a == 0) {
+        w[0] -= v[0] + v[2];
+        w[1] -= v[1] + v[3];
+    } else {
+        const int sp = a > 0 ? 0 : 2, sm = 2 - sp;
+        w[sp] -= v[0];
+        w[sp + 1] -= v[1];
+        w[sm] -= v[2];
+        w[sm + 1] -= v[3];
+    }
+}
+
 // The contraction's items (output tile, K-split), one per CTA and round; each stores its float64
 // partial.  `ok` turns false (for the whole CTA) when an mbarrier wait gives up.
 template <int NSL>
@@ -156,14 +223,64 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
     const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
     const int Nc = p.Nc, M = jb.M;
     const int items = jb.tiles * jb.splits;
-    __shared__ int s_eb[NT];   // scale exponents of the tile's B columns
+    __shared__ int s_eb[NT];        // scale exponents of the tile's B columns
+    __shared__ double s_row0[NT];   // solve: the tile's part of g_m's first row
+    __shared__ double s_v[NT];      // solve: order m+1's alias sums for that row
     for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
         const int tile = it / jb.splits, y = it - tile * jb.splits;
         const int tm = tile / jb.tiles_n, tn = tile - tm * jb.tiles_n;
         const int row0 = tm * MT, col0 = tn * NT;
         const int kbeg = y * jb.kchunk, kend = min(jb.K, kbeg + jb.kchunk);
         __syncthreads();   // the previous item's epilogue is done with s_eb
-        if (tid < NT) s_eb[tid] = col0 + tid < Nc ? scale_from_field(__ldcg(jb.eB + col0 + tid)) : 0;
+        if (jb.first) {
+            // ring m of the tile's 16 signals with order m+1's alias contribution removed (every
+            // item of a column computes the same values, hence the same column scale): one thread
+            // per column sums the alias partials exactly, then applies the bin mapping of EPI_ALIAS
+            const FirstRow &fr = *jb.first;
+            const int col = col0 + tid;
+            if (tid < NT) {
+                double v = 0.0;
+                if (fr.pending && col < Nc) {
+                    const Partials &pa = fr.alias;
+                    const int r = pa.M - 1;
+                    long long t = 0;
+                    for (int y0 = 0; y0 < pa.splits; y0 += 8) {
+                        long long a8[8];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            a8[u] = y0 + u < pa.splits ? __ldcg(pa.part + ((int64_t)(y0 + u) * pa.M + r) * Nc + col) : 0ll;
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) t += a8[u];
+                    }
+                    v = i64_scaled(t, pa.sc.eA[r] - pa.sc.shift + scale_from_field(__ldcg(pa.sc.fB + col)));
+                }
+                s_v[tid] = v;
+            }
+            __syncthreads();
+            if (tid < NT) {
+                double w = col < Nc ? __ldcg(jb.B + col) : 0.0;
+                if (fr.pending && col < Nc) {
+                    const int q = tid & 3, b0 = tid & ~3;
+                    if (fr.a == 0) {
+                        if (q < 2) w -= s_v[b0 + q] + s_v[b0 + q + 2];
+                    } else {
+                        const int sp = fr.a > 0 ? 0 : 2;   // slot of bin a: receives G_{+}
+                        w -= (q >> 1) == (sp >> 1) ? s_v[b0 + (q & 1)] : s_v[b0 + 2 + (q & 1)];
+                    }
+                }
+                s_row0[tid] = w;
+            }
+            __syncthreads();
+        }
+        if (tid < NT) {
+            const int col = col0 + tid;
+            int f = col < Nc ? __ldcg(jb.eB + col) : 0;
+            if (jb.first && col < Nc) {
+                f = max(f, exp_field(s_row0[tid]));
+                if (tm == 0 && y == 0) p.fS[col] = f;
+            }
+            s_eb[tid] = scale_from_field(f);
+        }
         __syncthreads();
 
         // k-block kb into stage st: the A slices (all S of them, 128 rows x 32 K, 64-byte
@@ -185,6 +302,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                 const int k = kbase + 2 * (h + 4 * (i >> 1)) + (i & 1);
                 x[i] = (col < Nc && k < kend) ? __ldcg(jb.B + (int64_t)k * Nc + col) : 0.0;
             }
+            if (jb.first && kbase == 0 && h == 0) x[0] = s_row0[j];   // row 0: g_m's completed first row
             const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -295,7 +413,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             for (int g = 0; g < kCols / 4; ++g) {
                 const int cl = half * kCols + 4 * g, c0 = col0 + cl;
                 if (c0 >= Nc) break;
-                long long *pp = p.part + ((int64_t)y * M + row) * Nc + c0;
+                long long *pp = jb.part + ((int64_t)y * M + row) * Nc + c0;
                 *reinterpret_cast<longlong2 *>(pp) = make_longlong2(acc[4 * g], acc[4 * g + 1]);
                 *reinterpret_cast<longlong2 *>(pp + 2) = make_longlong2(acc[4 * g + 2], acc[4 * g + 3]);
             }
@@ -303,92 +421,59 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
     }
 }
 
-// Exact int64 sum of the K-split partials of row r, columns c0..c0+3 (all at the scale of the
-// output element), then one conversion: 2^(eA_r + eB_c - shift) * sum.
-struct Scales {
-    const int *eA;     // row scale exponents
-    const int *fB;     // exponent fields of the right-hand side's columns
-    int shift;
-};
-__device__ __forceinline__ void sum_partials(const ChainArgs &p, const Scales &sc, int M, int splits, int r,
-                                             int c0, double v[4]) {
-    const int Nc = p.Nc;
-    long long t[4] = {0, 0, 0, 0};
-    for (int y0 = 0; y0 < splits; y0 += 8) {
-        longlong2 a[8], b[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (y0 + u < splits) {
-                const longlong2 *pp = reinterpret_cast<const longlong2 *>(p.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
-                a[u] = __ldcg(pp);
-                b[u] = __ldcg(pp + 1);
-            }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (y0 + u < splits) { t[0] += a[u].x; t[1] += a[u].y; t[2] += b[u].x; t[3] += b[u].y; }
-    }
-    const int er = sc.eA[r] - sc.shift;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = i64_scaled(t[q], er + scale_from_field(__ldcg(sc.fB + c0 + q)));
-}
-
-// Solve epilogue: F_m rows and f_l^{+-m}; largest exponent fields of F_m's columns into ef.
-// When the grid's thread count is a multiple of the column groups, every thread of a CTA stays on
-// one group and the CTA's groups are a window of kThreads groups: the maxima are first gathered in
-// shared memory, one global atomicMax per CTA and column.
-__device__ __noinline__ void reduce_solve(const ChainArgs &p, const EpiArgs &epi, const Scales &sc, int M,
-                                          int splits, int *ef) {
+// The reduction phase of order m:
+//  (a) the solve's partials -> F_m rows and f_l^{+-m}; largest exponent fields of F_m's columns
+//      into ef (gathered per CTA in shared memory when the grid's thread count is a multiple of
+//      the column groups: every thread then stays on one group and the CTA's groups are a window
+//      of kThreads groups; one global atomicMax per CTA and column);
+//  (b) order m+1's alias sums subtracted from the bins of rings k < m (ring m, the first row of
+//      g_m, was completed by the solve's items and is not needed again);
+//  (c) largest exponent fields of g_{m-1}'s columns over its rows 1.. (rings >= m: final, and
+//      untouched by (b)) into efw.
+__device__ __noinline__ void reduce_phase(const ChainArgs &p, const EpiArgs &es, const Partials &ps, int *ef,
+                                          bool prev, const EpiArgs &ea, const Partials &pa,
+                                          const double *gnext, int gnext_rows, int *efw) {
     const int groups = p.Nc / 4;
-    const int64_t total = (int64_t)M * groups, T = (int64_t)gridDim.x * kThreads;
-    __shared__ int s_ef[4 * kThreads];
-    const bool windowed = T % groups == 0;
-    const int g0 = (int)(((int64_t)blockIdx.x * kThreads) % groups);
-    const int span = min(groups, kThreads);
-    for (int i = threadIdx.x; i < 4 * kThreads; i += kThreads) s_ef[i] = 0;
-    __syncthreads();
-    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
-        const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
-        double v[4];
-        sum_partials(p, sc, M, splits, r, 4 * g, v);
-        epilogue_row4<EPI_SOLVE>(epi, r, 4 * g, v);
-        const int w = g - g0 < 0 ? g - g0 + groups : g - g0;   // position in the CTA's window
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int f = exp_field(v[q]);
-            if (f == 0) continue;
-            if (windowed) atomicMax(&s_ef[4 * w + q], f);
-            else atomicMax(ef + 4 * g + q, f);
-        }
-    }
-    __syncthreads();
-    if (windowed)
-        for (int i = threadIdx.x; i < 4 * span; i += kThreads) {
-            const int w = i >> 2, g = g0 + w < groups ? g0 + w : g0 + w - groups;
-            if (s_ef[i] > 0) atomicMax(ef + 4 * g + (i & 3), s_ef[i]);
-        }
-}
-
-// Alias epilogue: subtract from the bins of rings k < m; then the rows of g_{m-1} are final:
-// ring m - 1 (row 0 of block m - 1, just updated here by the thread that wrote it) and rings
-// m .. L-1 (rows 1 ..), whose largest exponent fields go to ef.
-__device__ __noinline__ void reduce_alias(const ChainArgs &p, const EpiArgs &epi, const Scales &sc, int m,
-                                          int splits, int *ef) {
-    const int L = p.L, Nc = p.Nc, groups = Nc / 4;
-    const int64_t total = (int64_t)m * groups, T = (int64_t)gridDim.x * kThreads;
-    const double *g1 = p.W + rows_off(L, m - 1) * Nc;   // block m - 1
-    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
-        const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
-        double v[4];
-        sum_partials(p, sc, m, splits, r, 4 * g, v);
-        epilogue_row4<EPI_ALIAS>(epi, r, 4 * g, v);
-        if (r == m - 1)
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    {
+        const int64_t total = (int64_t)ps.M * groups;
+        __shared__ int s_ef[4 * kThreads];
+        const bool windowed = T % groups == 0;
+        const int g0 = (int)(((int64_t)blockIdx.x * kThreads) % groups);
+        const int span = min(groups, kThreads);
+        for (int i = threadIdx.x; i < 4 * kThreads; i += kThreads) s_ef[i] = 0;
+        __syncthreads();
+        for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
+            const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
+            double v[4];
+            sum_partials(p, ps, r, 4 * g, v);
+            epilogue_row4<EPI_SOLVE>(es, r, 4 * g, v);
+            const int w = g - g0 < 0 ? g - g0 + groups : g - g0;   // position in the CTA's window
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int f = exp_field(__ldcg(g1 + 4 * g + q));
-                if (f > 0) atomicMax(ef + 4 * g + q, f);
+                const int f = exp_field(v[q]);
+                if (f == 0) continue;
+                if (windowed) atomicMax(&s_ef[4 * w + q], f);
+                else atomicMax(ef + 4 * g + q, f);
+            }
+        }
+        __syncthreads();
+        if (windowed)
+            for (int i = threadIdx.x; i < 4 * span; i += kThreads) {
+                const int w = i >> 2, g = g0 + w < groups ? g0 + w : g0 + w - groups;
+                if (s_ef[i] > 0) atomicMax(ef + 4 * g + (i & 3), s_ef[i]);
             }
     }
-    column_fields(p, g1 + Nc, L - m, ef);
+    if (prev) {
+        const int64_t total = (int64_t)(pa.M - 1) * groups;
+        for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
+            const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
+            double v[4];
+            sum_partials(p, pa, r, 4 * g, v);
+            epilogue_row4<EPI_ALIAS>(ea, r, 4 * g, v);
+        }
+    }
+    if (gnext) column_fields(p, gnext, gnext_rows, efw);
 }
 
 template <int NSL>
@@ -417,36 +502,52 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     unsigned target = 0;   // arrivals that complete the next grid barrier
     bool ok = true, mma_ok = true;
     const int L = p.L, Nc = p.Nc;
-    // column scales of g_{L-1}: the single ring L-1
-    column_fields(p, p.W + rows_off(L, L - 1) * Nc, 1, p.eW + ((L - 1) & 1) * Nc);
-    ok = grid_barrier(p, &s_flag, target);
-    for (int m = L - 1; m >= 0 && ok; --m) {
+    constexpr int SHIFT = NSL == S ? ACC_SHIFT : 40;
+    for (int m = L - 1; m >= 0; --m) {
         const int n = L - m, kp = (n + 7) & ~7, sl = m & 1;
-        // slots of order m - 1: no reader until after the next barrier (last read by order m + 1)
-        for (int j = blockIdx.x * kThreads + tid; j < Nc; j += gridDim.x * kThreads) {
-            p.eW[(sl ^ 1) * Nc + j] = 0;
-            p.eF[(sl ^ 1) * Nc + j] = 0;
+        // order m+1's alias products: their partials are still in part_a
+        FirstRow first;
+        first.pending = m + 1 < L;
+        first.a = 0;
+        first.alias = Partials{p.part_a, 0, 0, Scales{nullptr, nullptr, SHIFT}};
+        if (first.pending) {
+            const int n1 = n - 1;
+            const Job jp = make_job(nullptr, nullptr, (n1 + 7) & ~7, nullptr, nullptr, m + 1, n1, Nc);
+            first.alias = Partials{p.part_a, m + 1, jp.splits,
+                                   Scales{p.ptE + (int64_t)(m + 1) * L, p.eF + (sl ^ 1) * Nc, SHIFT}};
+            first.a = alias_bin(m + 1, m);
         }
         // Eq. (14): F_m = P_m^{-1} g_m
-        const Job js = make_job(p.tmaps + (size_t)(2 * m) * kTensorMapBytes, p.piE + rows_off(L, m), kp,
-                                p.W + rows_off(L, m) * Nc, p.eW + sl * Nc, n, n, Nc);
+        Job js = make_job(p.tmaps + (size_t)(2 * m) * kTensorMapBytes, p.piE + rows_off(L, m), kp,
+                          p.W + rows_off(L, m) * Nc, p.eW + sl * Nc, n, n, Nc);
+        js.part = p.part_s;
+        js.first = &first;
         mma_phase<NSL>(p, js, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
         if (!(ok = grid_barrier(p, &s_flag, target))) break;
-        const EpiArgs es{p.F + rows_off(L, m) * Nc, Nc, nullptr, m, L, Nc, p.coeffs, nullptr};
-        const Scales ss{js.eA, js.eB, NSL == S ? ACC_SHIFT : 40};
-        reduce_solve(p, es, ss, n, js.splits, p.eF + sl * Nc);
+        {
+            const EpiArgs es{p.F + rows_off(L, m) * Nc, Nc, nullptr, m, L, Nc, p.coeffs, nullptr};
+            const Partials ps{p.part_s, n, js.splits, Scales{js.eA, p.fS, SHIFT}};
+            const EpiArgs ea{nullptr, Nc, nullptr, m + 1, L, Nc, nullptr, p.W};
+            const double *gn = m >= 1 ? p.W + (rows_off(L, m - 1) + 1) * Nc : nullptr;
+            reduce_phase(p, es, ps, p.eF + sl * Nc, first.pending, ea, first.alias, gn, L - m,
+                         p.eW + (sl ^ 1) * Nc);
+        }
         if (!(ok = grid_barrier(p, &s_flag, target))) break;
         if (m == 0) break;
-        // Eqs. (15)-(16): orders +-m out of the bins of rings k < m
-        const Job ja = make_job(p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes, p.ptE + (int64_t)m * L, kp,
-                                p.F + rows_off(L, m) * Nc, p.eF + sl * Nc, m, n, Nc);
+        // slots read for the last time: eW of order m, eF of order m + 1 (next written by the
+        // reductions of orders m - 1 and m - 1)
+        for (int j = blockIdx.x * kThreads + tid; j < Nc; j += gridDim.x * kThreads) {
+            p.eW[sl * Nc + j] = 0;
+            p.eF[(sl ^ 1) * Nc + j] = 0;
+        }
+        // Eqs. (15)-(16): orders +-m out of the bins of rings k < m (partials only; summed and
+        // subtracted in the next order's phases)
+        Job ja = make_job(p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes, p.ptE + (int64_t)m * L, kp,
+                          p.F + rows_off(L, m) * Nc, p.eF + sl * Nc, m, n, Nc);
+        ja.part = p.part_a;
         mma_phase<NSL>(p, ja, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
-        if (!(ok = grid_barrier(p, &s_flag, target))) break;
-        const EpiArgs ea{nullptr, Nc, nullptr, m, L, Nc, nullptr, p.W};
-        const Scales sa{ja.eA, ja.eB, NSL == S ? ACC_SHIFT : 40};
-        reduce_alias(p, ea, sa, m, ja.splits, p.eW + (sl ^ 1) * Nc);
         if (!(ok = grid_barrier(p, &s_flag, target))) break;
     }
     if (!mma_ok) {
@@ -503,7 +604,7 @@ cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vec
     return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
 }
 
-int64_t tc_chain_words(int64_t batch) { return kChainBarWords + 16 * batch; }
+int64_t tc_chain_words(int64_t batch) { return kChainBarWords + 5 * 4 * batch; }
 
 cudaError_t tc_prepare_chain(int *grid) {
     cudaError_t e;
@@ -522,17 +623,19 @@ cudaError_t tc_prepare_chain(int *grid) {
 }
 
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, double *part, unsigned *words, int *status, int nsl,
-                             int grid, uint64_t wait_ns, cudaStream_t s) {
+                             double2 *coeffs, double *part, double *part2, unsigned *words, int *status,
+                             int nsl, int grid, uint64_t wait_ns, cudaStream_t s) {
     ChainArgs p{};
     p.L = L; p.Nc = (int)(4 * batch);
     p.W = W; p.F = F; p.coeffs = coeffs;
     p.piS = t.piS; p.piE = t.piE; p.pik_off = t.pik_off;
     p.ptS = t.ptS; p.ptE = t.ptE; p.ptk_off = t.ptk_off;
     p.tmaps = t.tmaps;
-    p.part = reinterpret_cast<long long *>(part); p.bar = words; p.status = status; p.wait_ns = wait_ns;
+    p.part_s = reinterpret_cast<long long *>(part); p.part_a = reinterpret_cast<long long *>(part2);
+    p.bar = words; p.status = status; p.wait_ns = wait_ns;
     p.eW = reinterpret_cast<int *>(words + kChainBarWords);
     p.eF = p.eW + 2 * p.Nc;
+    p.fS = p.eF + 2 * p.Nc;
     cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * tc_chain_words(batch), s);
     if (e != cudaSuccess) return e;
     if (nsl == S) return launch_chain<S>(p, grid, s);

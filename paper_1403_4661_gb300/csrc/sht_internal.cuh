@@ -79,6 +79,7 @@ struct Workspace {
     int *xE = nullptr;
     unsigned char *tmX = nullptr;    // tensor plans: TMA maps of the X slices
     unsigned *bar = nullptr;         // tensor plans: words of the chain kernel (tc_chain_words)
+    double *part2 = nullptr;         // tensor plans: the chain's alias partials (as `part`)
     double2 *r = nullptr, *dx = nullptr;  // refinement: residual, update
     uint64_t bytes = 0;
 };
@@ -226,8 +227,8 @@ cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vec
 constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 128-byte lines
 cudaError_t tc_prepare_chain(int *grid);
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, double *part, unsigned *words, int *status, int nsl,
-                             int grid, uint64_t wait_ns, cudaStream_t s);
+                             double2 *coeffs, double *part, double *part2, unsigned *words, int *status,
+                             int nsl, int grid, uint64_t wait_ns, cudaStream_t s);
 // Device words the chain kernel needs beside W, F and part (barrier, column scales).
 int64_t tc_chain_words(int64_t batch);
 // TMA maps of the per-call X slices (order m at m: {kp, 4B, S}, boxes 32 x 64 x S), written to a
