@@ -7,7 +7,8 @@ A step is one inverse SHT (coefficients -> samples) followed by one forward SHT 
 coefficients) of a batch of synthetic signals: every stage of the path (ring DFTs, the order
 chain with its solves and alias subtractions, the synthesis contraction, the fold and inverse
 ring DFTs) runs once per step.  Default workload: 64 complex signals at L = 1024, f_l^m re/im iid
-N(0,1) * (l+1)^-1, plain float64.  Inputs (1 GiB per buffer) are larger than L2.
+N(0,1) * (l+1)^-1, float64-accurate results with the contractions on the BF16 tensor cores from
+exact slices (--dtype f64 for the float64 pipe).  Inputs (1 GiB per buffer) are larger than L2.
 
 Under torchrun (N > 1) every rank transforms its own batch (weak scaling, no collective on the
 data path); the time is the max over ranks.
