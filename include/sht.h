@@ -65,12 +65,19 @@ typedef enum {
  *                   float64-accurate inverse of SHT_F64_TENSOR; the ring DFTs, the Legendre
  *                   recursion and the residual s - A x stay float64-accurate.  The inverse and the
  *                   adjoints are those of SHT_F64_TENSOR.  See sht_plan_set_refinement.
+ *   SHT_TF32_REFINED
+ *                   the same refinement with F_lo's contractions on the TF32 tensor cores
+ *                   (tcgen05 kind::tf32, FP32 accumulation): the table rows scaled by a power of two
+ *                   and rounded to TF32 at plan time (10 stored significand bits), the right-hand
+ *                   sides scaled per column and rounded to TF32 in the kernel.  The plan holds TF32
+ *                   copies of both tables (L^3/2 + L^3/3 floats) besides the SHT_F64_TENSOR slices.
  */
 typedef enum {
     SHT_F64 = 0,
     SHT_F64_TENSOR = 1,
     SHT_BF16_REFINED = 2,
-    SHT_BF16X2_REFINED = 3
+    SHT_BF16X2_REFINED = 3,
+    SHT_TF32_REFINED = 4
 } sht_dtype;
 
 /* Plan flags: ring ordering (Sec. III-E). */
@@ -197,7 +204,7 @@ sht_status sht_forward_noalloc(sht_plan_t plan, const void *d_samples, void *d_c
                                int64_t batch, void *stream);
 
 /*
- * sht_plan_set_refinement - iteration control of the refined forward (SHT_BF16*_REFINED plans).
+ * sht_plan_set_refinement - iteration control of the refined forward (SHT_*_REFINED plans).
  *   tol > 0: iterate until the largest |Re|, |Im| over the last update of the coefficients is
  *   <= tol, at most max_iters iterations; each iteration reads that maximum to the host
  *   (synchronises the call's stream); not reaching tol returns SHT_ERR_NOT_CONVERGED with the last

@@ -49,6 +49,7 @@ void destroy(sht_plan_t p) {
     cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
     cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
     cudaFree(p->d_tmaps);
+    cudaFree(p->ptT); cudaFree(p->piT); cudaFree(p->d_tmaps_tf32);
     dft_plan_destroy(p->dft);
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -131,6 +132,19 @@ sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
     if ((e = tc_table_tensor_maps(L, p->piS, p->pik_off, p->ptS, p->ptk_off, &p->d_tmaps)) != cudaSuccess)
         return cuda_check(e, "tensor maps of the table slices");
     bytes += (uint64_t)2 * L * kTensorMapBytes;
+    if (p->refine_tf32) {
+        // TF32 copies of both tables for the low-precision chain, rows scaled like the slices
+        const size_t ptt = sizeof(float) * (size_t)L * (size_t)p->ptk_off[L];
+        const size_t pit = sizeof(float) * (size_t)p->pik_off[L];
+        if ((e = cudaMalloc(&p->ptT, ptt)) != cudaSuccess || (e = cudaMalloc(&p->piT, pit)) != cudaSuccess)
+            return cuda_check(e, "TF32 table allocation");
+        if ((e = tc_tf32_table(p->pt, L, false, p->d_ptk_off, p->ptE, p->ptT, s)) != cudaSuccess ||
+            (e = tc_tf32_table(p->pinv, L, true, p->d_pik_off, p->piE, p->piT, s)) != cudaSuccess)
+            return cuda_check(e, "TF32 tables");
+        if ((e = tc_table_tensor_maps_tf32(L, p->piT, p->pik_off, p->ptT, p->ptk_off, &p->d_tmaps_tf32)) != cudaSuccess)
+            return cuda_check(e, "tensor maps of the TF32 tables");
+        bytes += ptt + pit + (uint64_t)2 * L * kTensorMapBytes;
+    }
     e = cudaStreamSynchronize(s);
     return cuda_check(e, "tensor-core table slices");
 }
@@ -183,6 +197,7 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
     }
     if (dtype == SHT_BF16_REFINED) p->refine_nsl = 1;
     if (dtype == SHT_BF16X2_REFINED) p->refine_nsl = 2;
+    if (dtype == SHT_TF32_REFINED) { p->refine_nsl = 1; p->refine_tf32 = true; }
     if (st == SHT_OK && dtype != SHT_F64) st = build_tensor_tables(p, s, tc_bytes);
     cudaStreamDestroy(s);
     if (st != SHT_OK) { destroy(p); *out = nullptr; return st; }
@@ -269,10 +284,12 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
     if (p->dtype != SHT_F64) {
         // Eqs. (14)-(16) for every order in one persistent launch (stage span: solve)
         Span sp(p, SHT_STAGE_SOLVE, s);
-        const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off, p->d_tmaps};
+        const bool tf32 = p->refine_tf32 && nsl < kTcSlices;   // the TF32 refinement's F_lo
+        const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off,
+                            tf32 ? p->d_tmaps_tf32 : p->d_tmaps};
         if (e == cudaSuccess)
             e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.part2, w.bar, p->d_status, nsl,
-                                 p->chain_grid, p->wait_ns, s);
+                                 tf32, p->chain_grid, p->wait_ns, s);
         p->launches += 1;
         return e;
     }
@@ -464,7 +481,7 @@ sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if ((int)dtype < 0 || (int)dtype > SHT_BF16X2_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if ((int)dtype < 0 || (int)dtype > SHT_TF32_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     if (!theta_host) return set_error(SHT_ERR_INVALID_ARG, "theta_host is NULL");
     std::vector<double> th(theta_host, theta_host + L);
     // the equiangular set's end point pi (2L-1)/(2L-1) may round one ulp past pi: allow 1e-12
@@ -477,7 +494,7 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if ((int)dtype < 0 || (int)dtype > SHT_BF16X2_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if ((int)dtype < 0 || (int)dtype > SHT_TF32_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     std::vector<int> order(L);
     auto t0 = std::chrono::steady_clock::now();
     if ((flags & SHT_ORDER_MASK) == SHT_ORDER_SIMPLE) {

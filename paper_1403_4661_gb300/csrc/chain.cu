@@ -212,13 +212,16 @@ __device__ __forceinline__ void alias_update(double w[4], int a, const double v[
     }
 }
 
-// The contraction's items (output tile, K-split), one per CTA and round; each stores its float64
+// The contraction's items (output tile, K-split), one per CTA and round; each stores its int64
 // partial.  `ok` turns false (for the whole CTA) when an mbarrier wait gives up.
-template <int NSL>
+// NSL BF16 slices per operand (kind::f16), or, with TF, one TF32 value per operand (kind::tf32:
+// the table rows pre-scaled and rounded at plan time, the right-hand side scaled by its column
+// scale and rounded here), accumulated in FP32 as the single-region low-precision path.
+template <int NSL, bool TF>
 __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32_t tbase,
                                        unsigned char *smem, uint64_t *mbar, uint64_t *full,
                                        uint32_t uses[2], uint32_t fills[2], bool &ok) {
-    constexpr bool EXACT = NSL == S;
+    constexpr bool EXACT = NSL == S && !TF;
     constexpr int NREG = EXACT ? REGIONS : 1;
     const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
     const int Nc = p.Nc, M = jb.M;
@@ -290,8 +293,15 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
             const int kbase = kb * KB;
             if (tid == 0) {
-                mbar_expect_tx(smem_u32(&full[st]), A_STAGE);
-                tma_load_3d(sa, jb.tmap, kbase, row0, 0, smem_u32(&full[st]));
+                if (TF) {
+                    // two boxes of 16 K (64 bytes) x 128 rows
+                    mbar_expect_tx(smem_u32(&full[st]), TF_A_STAGE);
+                    tma_load_2d(sa, jb.tmap, kbase, row0, smem_u32(&full[st]));
+                    tma_load_2d(sa + TF_A_HALF, jb.tmap, kbase + 16, row0, smem_u32(&full[st]));
+                } else {
+                    mbar_expect_tx(smem_u32(&full[st]), A_STAGE);
+                    tma_load_3d(sa, jb.tmap, kbase, row0, 0, smem_u32(&full[st]));
+                }
             }
             fills[st] += 1;
             const int j = tid & (NT - 1), h = tid >> 6, col = col0 + j;
@@ -304,6 +314,19 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             }
             if (jb.first && kbase == 0 && h == 0) x[0] = s_row0[j];   // row 0: g_m's completed first row
             const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
+            if (TF) {
+                // canonical K-major layout of 32-bit elements: core matrices of 8 columns x 4 K
+                // (16 bytes per column), NT * 16 bytes apart along K; rows kk, kk + 1 side by side
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = 2 * (h + 4 * q);
+                    const uint32_t a = cb + (kk >> 2) * (NT * 16) + (kk & 3) * 4;
+                    asm volatile("st.shared.v2.u32 [%0], {%1, %2};\n" ::"r"(a), "r"(tf32_scaled_bits(x[2 * q], e)),
+                                 "r"(tf32_scaled_bits(x[2 * q + 1], e))
+                                 : "memory");
+                }
+                return;
+            }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int kk = 2 * (h + 4 * q);
@@ -339,7 +362,17 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
                 bool fresh[REGIONS] = {false, false, false, false, false, false};
-                for (int hh = 0; hh < 2; ++hh) {
+                if (TF)
+                    for (int q = 0; q < 4; ++q) {
+                        // K = 8 per MMA: 32 bytes along a 64-byte swizzled A row, two core
+                        // matrices of B
+                        const int kg = kb * KB + 8 * q;
+                        if (kg >= kend) break;
+                        const uint64_t ad = sdesc_sw64(sa + (q >> 1) * TF_A_HALF + 32 * (q & 1));
+                        const uint64_t bd = sdesc(sb + 2 * q * (NT * 16), NT * 16, 128);
+                        mma_tf32(tbase, ad, bd, kIdescTf32, kg == kbeg ? 0u : 1u);
+                    }
+                for (int hh = 0; hh < 2 && !TF; ++hh) {
                     const int kg = kb * KB + 16 * hh;
                     if (kg >= kend) break;
                     if (kg == kbeg || (EXACT && kg % CHUNK == 0))
@@ -476,9 +509,9 @@ __device__ __noinline__ void reduce_phase(const ChainArgs &p, const EpiArgs &es,
     if (gnext) column_fields(p, gnext, gnext_rows, efw);
 }
 
-template <int NSL>
+template <int NSL, bool TF>
 __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
-    constexpr uint32_t NCOLS = NSL == S ? TMEM_COLS : 64u;
+    constexpr uint32_t NCOLS = NSL == S && !TF ? TMEM_COLS : 64u;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar[2];   // MMAs of a stage done
     __shared__ uint64_t full[2];   // TMA load of a stage landed
@@ -502,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     unsigned target = 0;   // arrivals that complete the next grid barrier
     bool ok = true, mma_ok = true;
     const int L = p.L, Nc = p.Nc;
-    constexpr int SHIFT = NSL == S ? ACC_SHIFT : 40;
+    constexpr int SHIFT = NSL == S && !TF ? ACC_SHIFT : 40;
     for (int m = L - 1; m >= 0; --m) {
         const int n = L - m, kp = (n + 7) & ~7, sl = m & 1;
         // order m+1's alias products: their partials are still in part_a
@@ -522,7 +555,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
                           p.W + rows_off(L, m) * Nc, p.eW + sl * Nc, n, n, Nc);
         js.part = p.part_s;
         js.first = &first;
-        mma_phase<NSL>(p, js, tbase, smem, mbar, full, uses, fills, mma_ok);
+        mma_phase<NSL, TF>(p, js, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
         if (!(ok = grid_barrier(p, &s_flag, target))) break;
         {
@@ -546,7 +579,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
         Job ja = make_job(p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes, p.ptE + (int64_t)m * L, kp,
                           p.F + rows_off(L, m) * Nc, p.eF + sl * Nc, m, n, Nc);
         ja.part = p.part_a;
-        mma_phase<NSL>(p, ja, tbase, smem, mbar, full, uses, fills, mma_ok);
+        mma_phase<NSL, TF>(p, ja, tbase, smem, mbar, full, uses, fills, mma_ok);
         if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
         if (!(ok = grid_barrier(p, &s_flag, target))) break;
     }
@@ -563,7 +596,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
     if (warp == 0) tmem_dealloc(tbase, NCOLS);
 }
 
-template <int NSL>
+template <int NSL, bool TF>
 cudaError_t launch_chain(const ChainArgs &p, int grid, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
@@ -575,7 +608,7 @@ cudaError_t launch_chain(const ChainArgs &p, int grid, cudaStream_t s) {
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_chain<NSL>, p);
+    return cudaLaunchKernelEx(&cfg, k_chain<NSL, TF>, p);
 }
 
 }  // namespace
@@ -604,18 +637,42 @@ cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vec
     return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
 }
 
+cudaError_t tc_table_tensor_maps_tf32(int L, const float *piT, const std::vector<int64_t> &pik_off,
+                                      const float *ptT, const std::vector<int64_t> &ptk_off,
+                                      unsigned char **d_maps) {
+    std::vector<CUtensorMap> maps((size_t)2 * L);
+    for (int m = 0; m < L; ++m) {
+        const int n = L - m;
+        const cuuint64_t kp = (cuuint64_t)((n + 7) & ~7);
+        for (int w = 0; w < 2; ++w) {
+            // w = 0: P_m^{-1} block (n rows); w = 1: P~ block (L rows); rows of kp floats
+            const cuuint64_t rows = w == 0 ? (cuuint64_t)n : (cuuint64_t)L;
+            const float *base = w == 0 ? piT + pik_off[m] : ptT + (int64_t)L * ptk_off[m];
+            const cuuint64_t dims[2] = {kp, rows};
+            const cuuint32_t box[2] = {16u, (cuuint32_t)MT};
+            const cudaError_t e = encode_tiled_map_f32(&maps[(size_t)2 * m + w], base, dims, kp * 4, box);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    const size_t bytes = maps.size() * sizeof(CUtensorMap);
+    const cudaError_t e = cudaMalloc(d_maps, bytes);
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
+}
+
 int64_t tc_chain_words(int64_t batch) { return kChainBarWords + 5 * 4 * batch; }
 
 cudaError_t tc_prepare_chain(int *grid) {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_chain<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_chain<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess ||
-        (e = cudaFuncSetAttribute(k_chain<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(k_chain<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_chain<2, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_chain<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_chain<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES)) != cudaSuccess)
         return e;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain<S>, kThreads, SMEM_BYTES)) != cudaSuccess)
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chain<S, false>, kThreads, SMEM_BYTES)) != cudaSuccess)
         return e;
     // one CTA per SM (the kernel holds the SM's tensor memory); never more than can be resident
     *grid = std::min(sms, sms * per_sm);
@@ -624,7 +681,7 @@ cudaError_t tc_prepare_chain(int *grid) {
 
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
                              double2 *coeffs, double *part, double *part2, unsigned *words, int *status,
-                             int nsl, int grid, uint64_t wait_ns, cudaStream_t s) {
+                             int nsl, bool tf32, int grid, uint64_t wait_ns, cudaStream_t s) {
     ChainArgs p{};
     p.L = L; p.Nc = (int)(4 * batch);
     p.W = W; p.F = F; p.coeffs = coeffs;
@@ -638,9 +695,10 @@ cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double 
     p.fS = p.eF + 2 * p.Nc;
     cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * tc_chain_words(batch), s);
     if (e != cudaSuccess) return e;
-    if (nsl == S) return launch_chain<S>(p, grid, s);
-    if (nsl == 2) return launch_chain<2>(p, grid, s);
-    if (nsl == 1) return launch_chain<1>(p, grid, s);
+    if (tf32) return launch_chain<1, true>(p, grid, s);
+    if (nsl == S) return launch_chain<S, false>(p, grid, s);
+    if (nsl == 2) return launch_chain<2, false>(p, grid, s);
+    if (nsl == 1) return launch_chain<1, false>(p, grid, s);
     return cudaErrorInvalidValue;
 }
 

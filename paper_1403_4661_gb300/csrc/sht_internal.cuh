@@ -108,13 +108,18 @@ struct sht_plan_s {
     int *ptE = nullptr, *piE = nullptr;
     int64_t *d_ptk_off = nullptr, *d_pik_off = nullptr;
     unsigned char *d_tmaps = nullptr;   // TMA maps of the sliced tables (chain kernel)
+    // SHT_TF32_REFINED: TF32 copies of the tables (rows scaled by the slices' row exponents) and
+    // their TMA maps, read by the low-precision chain
+    float *ptT = nullptr, *piT = nullptr;
+    unsigned char *d_tmaps_tf32 = nullptr;
+    bool refine_tf32 = false;
     std::vector<int64_t> ptk_off, pik_off;
     int *d_status = nullptr;
 
-    // refinement (SHT_BF16_REFINED, SHT_BF16X2_REFINED)
-    int chain_grid = 0;
-    uint64_t wait_ns = 1000000000ull;   // limit of the tensor kernels' waits (sht_plan_set_wait_limit)           // CTAs of the persistent order-chain kernel (tensor plans)
-    int refine_nsl = 0;           // slices of the low-precision forward; 0: no refinement
+    int chain_grid = 0;                 // CTAs of the persistent order-chain kernel (tensor plans)
+    uint64_t wait_ns = 1000000000ull;   // limit of the tensor kernels' waits (sht_plan_set_wait_limit)
+    // refinement (SHT_BF16_REFINED, SHT_BF16X2_REFINED, SHT_TF32_REFINED)
+    int refine_nsl = 0;           // slices of the low-precision forward (1 for TF32); 0: no refinement
     int refine_max_iters = 10;
     double refine_tol = 1e-11;
     int refine_iters = 0;
@@ -210,6 +215,11 @@ cudaError_t tc_slice_table(const double *tab, int L, bool inverses, const int64_
 // at m * 4B.
 cudaError_t tc_slice_orders(const double *X, int L, int64_t batch, const int64_t *koff,
                             __nv_bfloat16 *out, int *expo, cudaStream_t s);
+// TF32 copies of a plan table (layouts of tc_slice_table without the slice factor): row r of
+// block m = the row times 2^-expo[r] rounded to TF32, zero padded to kp; expo as written by
+// tc_slice_table.
+cudaError_t tc_tf32_table(const double *tab, int L, bool inverses, const int64_t *koff, const int *expo,
+                          float *out, cudaStream_t s);
 // The forward's whole order chain (m = L-1 .. 0: solves, alias products) as one persistent
 // cooperative launch of `grid` CTAs (tc_prepare_chain); W holds the ring bins on entry.
 struct ChainTables {
@@ -224,11 +234,15 @@ constexpr int kTensorMapBytes = 128;
 cudaError_t tc_table_tensor_maps(int L, const __nv_bfloat16 *piS, const std::vector<int64_t> &pik_off,
                                  const __nv_bfloat16 *ptS, const std::vector<int64_t> &ptk_off,
                                  unsigned char **d_maps);
+// The same for the TF32 tables: 2-D float32 maps {kp, rows}, boxes of 16 x 128, 64-byte swizzle.
+cudaError_t tc_table_tensor_maps_tf32(int L, const float *piT, const std::vector<int64_t> &pik_off,
+                                      const float *ptT, const std::vector<int64_t> &ptk_off,
+                                      unsigned char **d_maps);
 constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 128-byte lines
 cudaError_t tc_prepare_chain(int *grid);
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
                              double2 *coeffs, double *part, double *part2, unsigned *words, int *status,
-                             int nsl, int grid, uint64_t wait_ns, cudaStream_t s);
+                             int nsl, bool tf32, int grid, uint64_t wait_ns, cudaStream_t s);
 // Device words the chain kernel needs beside W, F and part (barrier, column scales).
 int64_t tc_chain_words(int64_t batch);
 // TMA maps of the per-call X slices (order m at m: {kp, 4B, S}, boxes 32 x 64 x S), written to a

@@ -77,6 +77,14 @@ __device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t ad, uint64_t bd, u
         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
         : "memory");
 }
+// D[tmem] (+)= A[smem] * B[smem]^T, M = 128, N = 64, K = 8, TF32 in, FP32 accumulate
+__device__ __forceinline__ void mma_tf32(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
                  : "memory");
@@ -142,9 +150,24 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *tmap, int 
         ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(mbar)
         : "memory");
 }
+// TMA tile load of a 2-D box (x innermost) into shared memory; completes on the mbarrier.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        ::"r"(dst), "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                             ((uint32_t)(MT >> 4) << 24);
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32 (format code 2), both K-major.
+constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                ((uint32_t)(MT >> 4) << 24);
+// TF32 operand tiles: a 32-K block of the table operand is two TMA boxes of 16 floats (64 bytes,
+// 64-byte swizzle) x 128 rows; the right-hand side block is 32 K x 64 columns of floats.
+constexpr int TF_A_HALF = MT * 16 * 4;     // 8 KiB
+constexpr int TF_A_STAGE = 2 * TF_A_HALF;  // 16 KiB (fits in A_STAGE)
+static_assert(TF_A_STAGE <= A_STAGE && NT * KB * 4 <= B_STAGE, "TF32 tiles fit the BF16 stages");
 
 // ---------------------------------------------------------------- slicing
 // Integer-only slicing (the float64 pipe is 1/64 of the integer rate): with the biased exponent
@@ -173,6 +196,21 @@ __device__ __forceinline__ void split_value(double x, int e, __nv_bfloat16 out[S
         // a * 2^-7s, exact in BF16 (7 significant bits)
         out[s - 1] = __float2bfloat16_rn(sgn * __int2float_rn(a) * __int_as_float((127 - BETA * s) << 23));
     }
+}
+
+// x * 2^-e rounded to TF32 (10 stored significand bits; nearest, ties away from zero), as the
+// bits of a float32 whose 13 low significand bits are zero.  Integer operations only.  |x| < 2^e
+// (e a row or column scale of scale_from_field), so the result is at most 1 in magnitude; values
+// below the float32 normal range (|x| < 2^(e-126)) become 0.
+__device__ __forceinline__ uint32_t tf32_scaled_bits(double x, int e) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int f = (int)((bits >> 52) & 0x7FF);
+    const uint32_t sgn = (uint32_t)(bits >> 63) << 31;
+    int fe = f - e - 1023 + 127;                       // float32 exponent field of x * 2^-e
+    if (f == 0 || fe <= 0) return sgn;
+    unsigned long long m10 = ((bits & 0xFFFFFFFFFFFFFull) + (1ull << 41)) >> 42;   // 10 bits + carry
+    if (m10 >> 10) { m10 = 0; ++fe; }
+    return sgn | ((uint32_t)fe << 23) | ((uint32_t)m10 << 13);
 }
 
 // Slicing of one row x[0..K) with input stride `step` (one warp): scale exponent, S slices, zero
@@ -213,6 +251,27 @@ inline cudaError_t encode_tiled_map(CUtensorMap *map, const __nv_bfloat16 *base,
     const cuuint32_t step[3] = {1, 1, 1};
     const CUresult r = reinterpret_cast<Encode>(fn)(
         map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16 *>(base), dims, strides, box, step,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Host: a 2-D float32 TMA map (dims[0] = K innermost, then rows), 64-byte swizzled boxes of
+// box[0] x box[1], zero fill outside the tensor.
+inline cudaError_t encode_tiled_map_f32(CUtensorMap *map, const float *base, const cuuint64_t dims[2],
+                                        cuuint64_t row_stride, const cuuint32_t box[2]) {
+    using Encode = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || fn == nullptr) return cudaErrorNotSupported;
+    const cuuint32_t step[2] = {1, 1};
+    const cuuint64_t strides[1] = {row_stride};
+    const CUresult r = reinterpret_cast<Encode>(fn)(
+        map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, step,
         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;

@@ -49,6 +49,22 @@ __global__ void k_slice_rows_orders(const double *__restrict__ tab, int L, bool 
     slice_row_warp(blk + (int64_t)row * n, 1, n, kp, ob + (int64_t)row * kp, (int64_t)rows * kp, eb + row);
 }
 
+// TF32 copies of the plan tables for the TF32 refined forward: row r of block m holds
+// P(r, k) * 2^-e_r rounded to TF32 (e_r the row's scale exponent from the BF16 slicing), zero
+// padded to kp; same block offsets as the slices without the slice factor.  One warp per row.
+__global__ void k_tf32_rows_orders(const double *__restrict__ tab, int L, bool inverses,
+                                   const int64_t *__restrict__ koff, const int *__restrict__ expo,
+                                   float *__restrict__ out) {
+    const int m = blockIdx.y, n = L - m, kp = (n + 7) & ~7;
+    const int rows = inverses ? n : L;
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= rows) return;
+    const double *x = tab + (inverses ? pinv_off(L, m) : pt_off(L, m)) + (int64_t)row * n;
+    const int e = expo[(inverses ? rows_off(L, m) : (int64_t)m * L) + row];
+    uint32_t *o = reinterpret_cast<uint32_t *>(out + koff[m] * (inverses ? 1 : L) + (int64_t)row * kp);
+    for (int k = threadIdx.x & 31; k < kp; k += 32) o[k] = k < n ? tf32_scaled_bits(x[k], e) : 0u;
+}
+
 // Column slicing: X has K rows and `cols` columns (row-major, ld); output row j = column j.
 // One block of 256 threads per 32 columns.
 __device__ __forceinline__ void slice_cols_block(const double *__restrict__ X, int64_t ld, int K,
@@ -272,6 +288,13 @@ cudaError_t tc_slice_table(const double *tab, int L, bool inverses, const int64_
                            __nv_bfloat16 *out, int *expo, cudaStream_t s) {
     dim3 grid((unsigned)cdiv(L, 8), L);
     k_slice_rows_orders<<<grid, 256, 0, s>>>(tab, L, inverses, koff, out, expo);
+    return cudaGetLastError();
+}
+
+cudaError_t tc_tf32_table(const double *tab, int L, bool inverses, const int64_t *koff, const int *expo,
+                          float *out, cudaStream_t s) {
+    dim3 grid((unsigned)cdiv(L, 8), L);
+    k_tf32_rows_orders<<<grid, 256, 0, s>>>(tab, L, inverses, koff, expo, out);
     return cudaGetLastError();
 }
 

@@ -25,8 +25,9 @@ SHT_F64 = 0
 SHT_F64_TENSOR = 1
 SHT_BF16_REFINED = 2
 SHT_BF16X2_REFINED = 3
+SHT_TF32_REFINED = 4
 DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR, "bf16_refined": SHT_BF16_REFINED,
-          "bf16x2_refined": SHT_BF16X2_REFINED}
+          "bf16x2_refined": SHT_BF16X2_REFINED, "tf32_refined": SHT_TF32_REFINED}
 SHT_ORDER_GREEDY = 0
 SHT_ORDER_SIMPLE = 1
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",

@@ -1,5 +1,6 @@
-"""Refined forward transforms (SHT_BF16_REFINED, SHT_BF16X2_REFINED): low-precision tensor-core
-contractions, float64-accurate residual, against the oracle.  Tolerance 1e-10 (refined forms)."""
+"""Refined forward transforms (SHT_BF16_REFINED, SHT_BF16X2_REFINED, SHT_TF32_REFINED):
+low-precision tensor-core contractions (BF16 slices, or TF32 on tcgen05 kind::tf32), float64-accurate
+residual, against the oracle.  Tolerance 1e-10 (refined forms)."""
 import numpy as np
 import pytest
 import torch
@@ -29,8 +30,8 @@ def _gpu(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(DEV)
 
 
-@pytest.mark.parametrize("dtype", ["bf16x2_refined", "bf16_refined"])
-@pytest.mark.parametrize("L,B", [(3, 1), (16, 2), (64, 2), (129, 1)])
+@pytest.mark.parametrize("dtype", ["bf16x2_refined", "bf16_refined", "tf32_refined"])
+@pytest.mark.parametrize("L,B", [(3, 1), (16, 2), (64, 2), (129, 1), (200, 5)])
 def test_refined_forward_matches_oracle(dtype, L, B):
     th = oracle_thetas(L)
     s = synth.uniform_samples(L, B, 700 + L)
@@ -62,9 +63,10 @@ def test_not_converged_is_reported():
     assert p.info()["refine_iterations"] == 1
 
 
-def test_fixed_iterations_capture_in_a_graph():
+@pytest.mark.parametrize("dtype", ["bf16x2_refined", "tf32_refined"])
+def test_fixed_iterations_capture_in_a_graph(dtype):
     L, B = 80, 2
-    p = _plan(L, "bf16x2_refined", iters=4, tol=0.0)
+    p = _plan(L, dtype, iters=4, tol=0.0)
     p.reserve(B)
     s = _gpu(synth.uniform_samples(L, B, 5))
     c = torch.empty_like(s)
@@ -85,10 +87,12 @@ def test_fixed_iterations_capture_in_a_graph():
     assert np.abs(ref.cpu().numpy() - osht.forward(s.cpu().numpy(), L, th)).max() <= 1e-10
 
 
-def test_refined_full_size_round_trip():
-    """BF16x2 refinement at the full size (single-slice BF16 does not converge at L = 1024: its
-    low-precision forward is too far from the inverse of A for the iteration to contract)."""
-    L, B, dtype = 1024, 64, "bf16x2_refined"
+@pytest.mark.parametrize("dtype", ["bf16x2_refined", "tf32_refined"])
+def test_refined_full_size_round_trip(dtype):
+    """BF16x2 and TF32 refinement at the full size (single-slice BF16 does not converge at
+    L = 1024: its low-precision forward is too far from the inverse of A for the iteration to
+    contract).  Measured: 8 iterations (BF16x2), 5 (TF32)."""
+    L, B = 1024, 64
     p = _plan(L, dtype)
     c = _gpu(synth.decaying_coeffs(L, B, 7))
     c2 = p.forward(p.inverse(c))
