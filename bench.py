@@ -195,12 +195,13 @@ def _config(args):
              "f64_tensor": "float64-accurate, contractions on the BF16 tensor cores from exact slices",
              "bf16_refined": "forward by iterative refinement with BF16 contractions, float64-accurate residual",
              "bf16x2_refined": "forward by iterative refinement with BF16x2 contractions, float64-accurate residual",
-             "tf32_refined": "forward by iterative refinement with TF32 contractions, float64-accurate residual"}
+             "tf32_refined": "forward by iterative refinement with TF32 contractions, float64-accurate residual",
+             "f32": "plain float32 (complex64 signals)"}
     return {"workload": f"{args.batch} complex signals at L={args.L}, f_lm re/im iid N(0,1)/(l+1); "
                         f"inverse SHT then forward SHT, {arith.get(getattr(args, 'dtype', 'f64'))}",
             "arithmetic": getattr(args, "dtype", "f64"),
             "L": args.L, "batch_per_gpu": args.batch, "ordering": "greedy (Sec. III-E)",
-            "l2": "inputs larger than L2 (16 L^2 B bytes per buffer), no flush",
+            "l2": "inputs larger than L2 (16 L^2 B bytes per buffer, 8 L^2 B for f32), no flush",
             "e2e": "pinned host -> device copy of each step's batch and device -> host copy of its result, "
                    "on a second stream with two device buffer sets (overlapping the neighbouring steps)",
             "launch": "one CUDA graph per step" if not getattr(args, "no_graph", False) else "eager"}
@@ -239,7 +240,8 @@ def run_ours(args):
         elif not args.no_graph:
             args.no_graph = True  # tolerance-driven refinement synchronises each iteration
     plan.reserve(B)
-    c_host = torch.from_numpy(synth.decaying_coeffs(L, B, 1000 + rank)).pin_memory()
+    cdtype = torch.complex64 if args.dtype == "f32" else torch.complex128
+    c_host = torch.from_numpy(synth.decaying_coeffs(L, B, 1000 + rank)).to(cdtype).pin_memory()
     c = c_host.to(dev)
     s = torch.empty_like(c)
     c2 = torch.empty_like(c)
@@ -382,7 +384,16 @@ def run_ours(args):
     bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
     bf16_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks.get("bf16_tflops_sustained")
                 else "fallback 1.7 PFLOP/s sustained bf16")
-    if args.dtype != "f64":
+    if args.dtype == "f32":
+        # float32 plans: the synthesis contraction on the FP32 pipe (FFMA32): 128 lanes per SM
+        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = syn_flops / syn_sec / 1e12
+        roof = {"bound": "alu",
+                "kernel": "k_gemm<float,64,64,4,...,MODE_SYNTH> (float32 synthesis, Eq. (11))",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": f"GB300 FP32 pipe: 152 SMs x 128 lanes x 2 flops at the measured median {sm_mhz:.0f} MHz",
+                "traffic": _traffic_record("synthesis_f32", L, B)}
+    elif args.dtype != "f64":
         ch_ms, ch_n = stages["solve"]
         ch_sec = ch_ms / ch_n * 1e-3
         # 36 BF16 slice-pair products per float64 product (8 slices a side, s + t <= 9); the TF32
@@ -423,7 +434,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"f64": "f64", "f64_tensor": "f64 (bf16 tensor-core slices)",
+        "dtype": {"f64": "f64", "f64_tensor": "f64 (bf16 tensor-core slices)", "f32": "f32",
                   "tf32_refined": "tf32 contractions + f64 residual (refined)"}.get(
             args.dtype, "bf16 contractions + f64 residual (refined)"),
         "data": "synthetic",
@@ -432,7 +443,8 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": _whole_job_rate(ws, B, ms_e2e), "unit": "signals/s",
-                "h2d_bytes_per_step": 16 * L * L * B, "d2h_bytes_per_step": 16 * L * L * B},
+                "h2d_bytes_per_step": c_host.element_size() * L * L * B,
+                "d2h_bytes_per_step": c_host.element_size() * L * L * B},
         "clocks": clk,
         "gpu_launches": launches,
         "plan_seconds": plan_s,
@@ -450,7 +462,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--dtype", default="f64_tensor",
-                    choices=["f64", "f64_tensor", "bf16_refined", "bf16x2_refined", "tf32_refined"])
+                    choices=["f64", "f64_tensor", "bf16_refined", "bf16x2_refined", "tf32_refined", "f32"])
     ap.add_argument("--refine-iters", type=int, default=0,
                     help="refined forms: fixed iteration count (0: iterate to 1e-12)")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of one CUDA graph per step")

@@ -12,8 +12,11 @@
  *  Basis (Appendix A, Eq. (29)): orthonormal Y_l^m with the Condon-Shortley phase;
  *    P~_l^m(theta) = Y_l^m(theta, 0).
  *  Element type: complex128, interleaved (re, im) doubles - the layout of torch.complex128 and
- *    C99 double _Complex.  A batch of B signals is B consecutive blocks of L^2 elements.
- *  Device pointers must be 16-byte aligned; input and output must not overlap.
+ *    C99 double _Complex - for every plan arithmetic but SHT_F32, whose signals are complex64
+ *    (interleaved floats, torch.complex64).  A batch of B signals is B consecutive blocks of L^2
+ *    elements.
+ *  Device pointers must be aligned to one element (16 bytes; 8 for SHT_F32); input and output
+ *    must not overlap.
  *  Ownership: the caller owns every buffer it passes.  The plan owns its tables (the P~ table and
  *    the per-order inverses, allocated at plan creation) and its workspaces (allocated on the
  *    first call that needs them, or by sht_plan_reserve, and kept until sht_plan_destroy).
@@ -71,13 +74,21 @@ typedef enum {
  *                   and rounded to TF32 at plan time (10 stored significand bits), the right-hand
  *                   sides scaled per column and rounded to TF32 in the kernel.  The plan holds TF32
  *                   copies of both tables (L^3/2 + L^3/3 floats) besides the SHT_F64_TENSOR slices.
+ *   SHT_F32         every step in float32 on the FP32 pipe (the float64 kernels instantiated for
+ *                   float), complex64 samples and coefficients.  The Legendre table, the per-order
+ *                   inverses and the ring-DFT tables are computed in float64 at plan time and rounded
+ *                   to float32.  Errors are those of float32 arithmetic amplified as in float64
+ *                   (about 1e-6 relative to the largest coefficient at L = 64, growing with L).
+ *                   Refinement does not apply; sht_forward_noalloc and the uneven calls do not take
+ *                   SHT_F32 plans (SHT_ERR_UNSUPPORTED).
  */
 typedef enum {
     SHT_F64 = 0,
     SHT_F64_TENSOR = 1,
     SHT_BF16_REFINED = 2,
     SHT_BF16X2_REFINED = 3,
-    SHT_TF32_REFINED = 4
+    SHT_TF32_REFINED = 4,
+    SHT_F32 = 5
 } sht_dtype;
 
 /* Plan flags: ring ordering (Sec. III-E). */

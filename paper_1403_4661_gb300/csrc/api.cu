@@ -50,6 +50,7 @@ void destroy(sht_plan_t p) {
     cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
     cudaFree(p->d_tmaps);
     cudaFree(p->ptT); cudaFree(p->piT); cudaFree(p->d_tmaps_tf32);
+    cudaFree(p->ptF); cudaFree(p->pinvF);
     dft_plan_destroy(p->dft);
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
         for (auto &pr : p->spans[st]) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -60,7 +61,13 @@ void destroy(sht_plan_t p) {
     delete p;
 }
 
-// Scratch of one workspace for `batch` signals (grows, never shrinks).
+// Plans whose contractions run on the tensor cores (every arithmetic but SHT_F64 and SHT_F32).
+bool tensor_plan(sht_plan_t p) { return p->dtype != SHT_F64 && p->dtype != SHT_F32; }
+// Bytes of one complex element of the plan's signals (complex64 for SHT_F32, else complex128).
+int64_t elem_bytes(sht_plan_t p) { return p->dtype == SHT_F32 ? 8 : 16; }
+
+// Scratch of one workspace for `batch` signals (grows, never shrinks).  SHT_F32 plans use the
+// same buffers as float arrays.
 sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
     if (batch <= w.batch) return SHT_OK;
     free_ws(w);
@@ -80,7 +87,7 @@ sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
         if (e == cudaSuccess) e = cudaMalloc(&w.dx, io);
         bytes += 2 * io;
     }
-    if (e == cudaSuccess && p->dtype != SHT_F64) {
+    if (e == cudaSuccess && tensor_plan(p)) {
         const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
         const size_t words = sizeof(unsigned) * (size_t)tc_chain_words(batch);
         e = cudaMalloc(&w.xS, xs);
@@ -198,10 +205,24 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
     if (dtype == SHT_BF16_REFINED) p->refine_nsl = 1;
     if (dtype == SHT_BF16X2_REFINED) p->refine_nsl = 2;
     if (dtype == SHT_TF32_REFINED) { p->refine_nsl = 1; p->refine_tf32 = true; }
-    if (st == SHT_OK && dtype != SHT_F64) st = build_tensor_tables(p, s, tc_bytes);
+    uint64_t f32_bytes = 0;
+    if (st == SHT_OK && dtype == SHT_F32) {
+        // float32 copies of the float64 tables (both are computed in float64 first)
+        const int64_t npt = pt_off(L, L), npi = pinv_off(L, L);
+        uint64_t dft_f = 0;
+        if ((e = cudaMalloc(&p->ptF, sizeof(float) * npt)) == cudaSuccess &&
+            (e = cudaMalloc(&p->pinvF, sizeof(float) * npi)) == cudaSuccess &&
+            (e = table_to_f32(p->pt, p->ptF, npt, s)) == cudaSuccess &&
+            (e = table_to_f32(p->pinv, p->pinvF, npi, s)) == cudaSuccess &&
+            (e = dft_plan_make_f32(L, p->dft, dft_f, s)) == cudaSuccess)
+            e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_check(e, "float32 tables");
+        f32_bytes = sizeof(float) * (uint64_t)(npt + npi) + dft_f;
+    }
+    if (st == SHT_OK && tensor_plan(p)) st = build_tensor_tables(p, s, tc_bytes);
     cudaStreamDestroy(s);
     if (st != SHT_OK) { destroy(p); *out = nullptr; return st; }
-    p->table_bytes = pt_bytes + pi_bytes + dft_bytes + tc_bytes + sizeof(double) * L;
+    p->table_bytes = pt_bytes + pi_bytes + dft_bytes + tc_bytes + f32_bytes + sizeof(double) * L;
     p->plan_seconds = order_s + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
     return SHT_OK;
@@ -259,21 +280,173 @@ sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch
     if (batch < 0 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [0, 65535]");
     if (batch == 0) return SHT_OK;
     if (!in || !out) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");
-    if (((uintptr_t)in & 15u) || ((uintptr_t)out & 15u))
-        return set_error(SHT_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
-    const uintptr_t bytes = (uintptr_t)16 * (uintptr_t)p->L * (uintptr_t)p->L * (uintptr_t)batch;
+    const uintptr_t eb = (uintptr_t)elem_bytes(p);   // alignment: one complex element
+    if (((uintptr_t)in & (eb - 1)) || ((uintptr_t)out & (eb - 1)))
+        return set_error(SHT_ERR_INVALID_ARG, eb == 16 ? "buffers must be 16-byte aligned"
+                                                       : "buffers must be 8-byte aligned");
+    const uintptr_t bytes = eb * (uintptr_t)p->L * (uintptr_t)p->L * (uintptr_t)batch;
     const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
     if (a < b + bytes && b < a + bytes) return set_error(SHT_ERR_INVALID_ARG, "input and output overlap");
     return SHT_OK;
 }
 
-// Forward transform (Procedure 1 in bin space).  Float64 plans run the float64 kernels; the other
-// plans run the contractions on the tensor cores with `nsl` slices per operand (kTcSlices:
+// SIMT contractions of the float64 (T = double) and float32 (T = float) plans: tables and GEMM.
+template <typename T> const T *pt_table(sht_plan_t p);
+template <> const double *pt_table<double>(sht_plan_t p) { return p->pt; }
+template <> const float *pt_table<float>(sht_plan_t p) { return p->ptF; }
+template <typename T> const T *pinv_table(sht_plan_t p);
+template <> const double *pinv_table<double>(sht_plan_t p) { return p->pinv; }
+template <> const float *pinv_table<float>(sht_plan_t p) { return p->pinvF; }
+cudaError_t gemm_simt(bool tA, int M, int K, int N, const double *A, int64_t lda, const double *B, int64_t ldb,
+                      double *C, int64_t ldc, int epi, const GemmArgsT<double> &ga, cudaStream_t s,
+                      const double *C0 = nullptr) {
+    return gemm_f64(tA, M, K, N, A, lda, B, ldb, C, ldc, epi, ga, s, C0);
+}
+cudaError_t gemm_simt(bool tA, int M, int K, int N, const float *A, int64_t lda, const float *B, int64_t ldb,
+                      float *C, int64_t ldc, int epi, const GemmArgsT<float> &ga, cudaStream_t s,
+                      const float *C0 = nullptr) {
+    return gemm_f32(tA, M, K, N, A, lda, B, ldb, C, ldc, epi, ga, s, C0);
+}
+
+// Eqs. (14)-(16) on the SIMT pipes, one solve and one alias product per order, m = L-1..0; W holds
+// the ring bins on entry.
+template <typename T>
+cudaError_t simt_chain(sht_plan_t p, Workspace &w, T *W, cplx_t<T> *d_coeffs, int64_t batch, cudaStream_t s) {
+    const int L = p->L;
+    const int64_t Nc = 4 * batch;
+    T *F = reinterpret_cast<T *>(w.b);
+    const T *pt = pt_table<T>(p), *pinv = pinv_table<T>(p);
+    cudaError_t e = cudaSuccess;
+    GemmArgsT<T> ga{};
+    ga.L = L; ga.batch = batch; ga.coeffs = d_coeffs; ga.W = W;
+    ga.part = reinterpret_cast<T *>(w.part); ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.launches = &p->launches;
+    for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
+        const int n = L - m;
+        ga.m = m;
+        {   // Eq. (14): F_m = P_m^{-1} g_m, with g_m = bins +-m of rings k >= m (alias-free by now)
+            Span sp(p, SHT_STAGE_SOLVE, s);
+            e = gemm_simt(false, n, n, (int)Nc, pinv + pinv_off(L, m), n, W + rows_off(L, m) * Nc,
+                          Nc, F + rows_off(L, m) * Nc, Nc, EPI_SOLVE, ga, s);
+        }
+        if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): remove orders +-m from rings k < m
+            Span sp(p, SHT_STAGE_ALIAS, s);
+            e = gemm_simt(false, m, n, (int)Nc, pt + pt_off(L, m), n, F + rows_off(L, m) * Nc, Nc,
+                          (T *)nullptr, Nc, EPI_ALIAS, ga, s);
+        }
+    }
+    return e;
+}
+
+// Forward transform of a float32 plan: ring DFTs into bins, then the SIMT chain, all in float32.
+cudaError_t forward_f32(sht_plan_t p, Workspace &w, const float2 *d_samples, float2 *d_coeffs,
+                        int64_t batch, cudaStream_t s) {
+    float *W = reinterpret_cast<float *>(w.a);
+    cudaError_t e;
+    {
+        Span sp(p, SHT_STAGE_RING_DFT, s);
+        e = ring_dft_to_bins(p->L, p->dft, d_samples, W, batch, true, s);
+    }
+    p->launches += ring_launches(p->L);
+    if (e == cudaSuccess) e = simt_chain<float>(p, w, W, d_coeffs, batch, s);
+    return e;
+}
+
+// Inverse transform on the SIMT pipes (float64 and float32 plans): layout, synthesis, fold + DFTs.
+template <typename T>
+cudaError_t simt_inverse(sht_plan_t p, Workspace &w, const cplx_t<T> *d_coeffs, cplx_t<T> *d_samples,
+                         int64_t batch, cudaStream_t s) {
+    const int L = p->L;
+    T *X = reinterpret_cast<T *>(w.a), *G = reinterpret_cast<T *>(w.g);
+    cudaError_t e;
+    {
+        Span sp(p, SHT_STAGE_LAYOUT, s);
+        e = coeffs_to_orders(L, batch, d_coeffs, X, s);
+    }
+    if (e == cudaSuccess) {  // Eq. (11): G_{+-m}(theta_k) for every order and ring
+        Span sp(p, SHT_STAGE_SYNTHESIS, s);
+        e = synthesis_all_orders(L, batch, pt_table<T>(p), X, G, s);
+    }
+    if (e == cudaSuccess) {  // Eq. (18): fold into ring bins, inverse ring DFTs
+        Span sp(p, SHT_STAGE_RING_IDFT, s);
+        e = fold_ring_idft(L, p->dft, G, d_samples, batch, s);
+    }
+    p->launches += 2 + ring_launches(L);
+    return e;
+}
+
+// Adjoint of the inverse (A^H): forward ring DFTs unfolded to every order, the transposed
+// synthesis, layout back to coefficients.
+template <typename T>
+cudaError_t simt_inverse_adjoint(sht_plan_t p, const cplx_t<T> *d_samples, cplx_t<T> *d_coeffs, int64_t batch,
+                                 cudaStream_t s) {
+    const int L = p->L;
+    T *G = reinterpret_cast<T *>(p->ws.g), *X = reinterpret_cast<T *>(p->ws.a);
+    cudaError_t e;
+    {
+        Span sp(p, SHT_STAGE_RING_DFT, s);
+        e = ring_dft_unfold(L, p->dft, d_samples, G, batch, s);
+    }
+    if (e == cudaSuccess) {
+        Span sp(p, SHT_STAGE_SYNTHESIS, s);
+        e = analysis_all_orders(L, batch, pt_table<T>(p), G, X, s);
+    }
+    if (e == cudaSuccess) {
+        Span sp(p, SHT_STAGE_LAYOUT, s);
+        e = orders_to_coeffs(L, batch, X, d_coeffs, s);
+    }
+    p->launches += 2 + ring_launches(L);
+    return e;
+}
+
+// Adjoint of the forward ((A^{-1})^H): the order chain in reverse (m = 0..L-1) with transposed
+// per-order inverses and alias gathers, then the adjoint ring DFTs.
+template <typename T>
+cudaError_t simt_forward_adjoint(sht_plan_t p, const cplx_t<T> *d_coeffs, cplx_t<T> *d_samples, int64_t batch,
+                                 cudaStream_t s) {
+    const int L = p->L;
+    const int64_t Nc = 4 * batch;
+    T *X = reinterpret_cast<T *>(p->ws.b), *W = reinterpret_cast<T *>(p->ws.a), *U = reinterpret_cast<T *>(p->ws.g);
+    const T *pt = pt_table<T>(p), *pinv = pinv_table<T>(p);
+    cudaError_t e;
+    {
+        Span sp(p, SHT_STAGE_LAYOUT, s);
+        e = coeffs_to_orders(L, batch, d_coeffs, X, s);
+    }
+    GemmArgsT<T> ga{};
+    ga.L = L; ga.batch = batch;
+    ga.part = reinterpret_cast<T *>(p->ws.part); ga.part_cap = (int64_t)kSplitCap * L * Nc;
+    ga.launches = &p->launches;
+    for (int m = 0; m < L && e == cudaSuccess; ++m) {
+        const int n = L - m;
+        T *Xm = X + rows_off(L, m) * Nc;
+        if (m > 0) {
+            // adjoint of the alias subtraction: X_m -= Q_m^T U, U[k] = bins alias_k(+-m) of rings k < m
+            Span sp(p, SHT_STAGE_ALIAS, s);
+            e = gather_alias_bins(L, m, batch, W, U, s);
+            if (e == cudaSuccess)
+                e = gemm_simt(true, n, m, (int)Nc, pt + pt_off(L, m), n, U, Nc, Xm, Nc, EPI_SUB, ga, s, Xm);
+        }
+        if (e == cudaSuccess) {  // adjoint of the solve: bins +-m of rings k >= m = P_m^{-T} X_m
+            Span sp(p, SHT_STAGE_SOLVE, s);
+            e = gemm_simt(true, n, n, (int)Nc, pinv + pinv_off(L, m), n, Xm, Nc, W + rows_off(L, m) * Nc, Nc,
+                          EPI_STORE, ga, s);
+        }
+    }
+    if (e == cudaSuccess) {
+        Span sp(p, SHT_STAGE_RING_IDFT, s);
+        e = bins_to_ring_adjoint(L, p->dft, W, d_samples, batch, s);
+    }
+    p->launches += 1 + (L - 1) + ring_launches(L);  // layout, alias gathers, ring DFTs
+    return e;
+}
+
+// Forward transform (Procedure 1 in bin space).  Float64 plans run the float64 kernels; the
+// tensor plans run the contractions on the tensor cores with `nsl` slices per operand (kTcSlices:
 // float64-accurate; fewer: the low-precision forward of the refinement).
 cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, double2 *d_coeffs,
                          int64_t batch, cudaStream_t s, int nsl) {
     const int L = p->L;
-    const int64_t Nc = 4 * batch;
     double *W = w.a, *F = w.b;
     cudaError_t e;
     {
@@ -281,7 +454,7 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         e = ring_dft_to_bins(L, p->dft, d_samples, W, batch, true, s);
     }
     p->launches += ring_launches(L);
-    if (p->dtype != SHT_F64) {
+    if (tensor_plan(p)) {
         // Eqs. (14)-(16) for every order in one persistent launch (stage span: solve)
         Span sp(p, SHT_STAGE_SOLVE, s);
         const bool tf32 = p->refine_tf32 && nsl < kTcSlices;   // the TF32 refinement's F_lo
@@ -293,30 +466,14 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         p->launches += 1;
         return e;
     }
-    GemmArgs ga{};
-    ga.L = L; ga.batch = batch; ga.coeffs = d_coeffs; ga.W = W;
-    ga.part = w.part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
-    ga.launches = &p->launches;
-    for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
-        const int n = L - m;
-        ga.m = m;
-        {   // Eq. (14): F_m = P_m^{-1} g_m, with g_m = bins +-m of rings k >= m (alias-free by now)
-            Span sp(p, SHT_STAGE_SOLVE, s);
-            e = gemm_f64(false, n, n, (int)Nc, p->pinv + pinv_off(L, m), n, W + rows_off(L, m) * Nc,
-                         Nc, F + rows_off(L, m) * Nc, Nc, EPI_SOLVE, ga, s);
-        }
-        if (m > 0 && e == cudaSuccess) {  // Eqs. (15)-(16): remove orders +-m from rings k < m
-            Span sp(p, SHT_STAGE_ALIAS, s);
-            e = gemm_f64(false, m, n, (int)Nc, p->pt + pt_off(L, m), n, F + rows_off(L, m) * Nc, Nc,
-                         nullptr, Nc, EPI_ALIAS, ga, s);
-        }
-    }
+    if (e == cudaSuccess) e = simt_chain<double>(p, w, W, d_coeffs, batch, s);
     return e;
 }
 
-// Inverse transform (Procedure 2), float64-accurate for every plan arithmetic.
+// Inverse transform (Procedure 2), float64-accurate for every plan arithmetic but SHT_F32.
 cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, double2 *d_samples,
                          int64_t batch, cudaStream_t s) {
+    if (!tensor_plan(p)) return simt_inverse<double>(p, w, d_coeffs, d_samples, batch, s);
     const int L = p->L;
     cudaError_t e;
     {
@@ -325,15 +482,11 @@ cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, do
     }
     if (e == cudaSuccess) {  // Eq. (11): G_{+-m}(theta_k) for every order and ring
         Span sp(p, SHT_STAGE_SYNTHESIS, s);
-        if (p->dtype != SHT_F64) {
-            e = tc_slice_orders(w.a, L, batch, p->d_ptk_off, w.xS, w.xE, s);
-            if (e == cudaSuccess)
-                e = tc_synthesis_all_orders(L, batch, p->ptE, p->d_tmaps, w.xE, w.tmX, w.g, p->d_status,
-                                            p->wait_ns, s);
-            p->launches += 1;
-        } else {
-            e = synthesis_all_orders(L, batch, p->pt, w.a, w.g, s);
-        }
+        e = tc_slice_orders(w.a, L, batch, p->d_ptk_off, w.xS, w.xE, s);
+        if (e == cudaSuccess)
+            e = tc_synthesis_all_orders(L, batch, p->ptE, p->d_tmaps, w.xE, w.tmX, w.g, p->d_status,
+                                        p->wait_ns, s);
+        p->launches += 1;
     }
     if (e == cudaSuccess) {  // Eq. (18): fold into ring bins, inverse ring DFTs
         Span sp(p, SHT_STAGE_RING_IDFT, s);
@@ -391,6 +544,8 @@ sht_status uneven(bool forward, const sht_plan_t *plans, int nplans, int64_t nsi
     for (int g = 0; g < nplans; ++g) {
         sht_status st = check_plan(plans[g]);
         if (st != SHT_OK) return st;
+        if (plans[g]->dtype == SHT_F32)
+            return set_error(SHT_ERR_UNSUPPORTED, "uneven batches take complex128 plans (not SHT_F32)");
     }
     // signals as intervals [offset, offset + L^2) of complex elements: in range, disjoint
     std::vector<std::pair<int64_t, int64_t>> iv((size_t)nsig);
@@ -481,7 +636,7 @@ sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if ((int)dtype < 0 || (int)dtype > SHT_TF32_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     if (!theta_host) return set_error(SHT_ERR_INVALID_ARG, "theta_host is NULL");
     std::vector<double> th(theta_host, theta_host + L);
     // the equiangular set's end point pi (2L-1)/(2L-1) may round one ulp past pi: allow 1e-12
@@ -494,7 +649,7 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if ((int)dtype < 0 || (int)dtype > SHT_TF32_REFINED) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     std::vector<int> order(L);
     auto t0 = std::chrono::steady_clock::now();
     if ((flags & SHT_ORDER_MASK) == SHT_ORDER_SIMPLE) {
@@ -610,6 +765,8 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->dtype == SHT_F32)
+        return cuda_check(forward_f32(p, p->ws, (const float2 *)d_samples, (float2 *)d_coeffs, batch, s), "sht_forward");
     if (p->refine_nsl > 0) return refined_forward(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s);
     return cuda_check(forward_impl(p, p->ws, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s,
                                    kTcSlices),
@@ -621,6 +778,10 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     sht_status st = check_io(p, d_coeffs, d_samples, batch);
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
+    if (p->dtype == SHT_F32)
+        return cuda_check(simt_inverse<float>(p, p->ws, (const float2 *)d_coeffs, (float2 *)d_samples, batch,
+                                              (cudaStream_t)stream),
+                          "sht_inverse");
     return cuda_check(inverse_impl(p, p->ws, (const double2 *)d_coeffs, (double2 *)d_samples, batch,
                                    (cudaStream_t)stream),
                       "sht_inverse");
@@ -642,21 +803,10 @@ sht_status sht_inverse_adjoint(sht_plan_t p, const void *d_samples, void *d_coef
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int L = p->L;
-    cudaError_t e;
-    {
-        Span sp(p, SHT_STAGE_RING_DFT, s);
-        e = ring_dft_unfold(L, p->dft, (const double2 *)d_samples, p->ws.g, batch, s);
-    }
-    if (e == cudaSuccess) {
-        Span sp(p, SHT_STAGE_SYNTHESIS, s);
-        e = analysis_all_orders(L, batch, p->pt, p->ws.g, p->ws.a, s);
-    }
-    if (e == cudaSuccess) {
-        Span sp(p, SHT_STAGE_LAYOUT, s);
-        e = orders_to_coeffs(L, batch, p->ws.a, (double2 *)d_coeffs, s);
-    }
-    p->launches += 2 + ring_launches(L);
+    const cudaError_t e =
+        p->dtype == SHT_F32
+            ? simt_inverse_adjoint<float>(p, (const float2 *)d_samples, (float2 *)d_coeffs, batch, s)
+            : simt_inverse_adjoint<double>(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s);
     return cuda_check(e, "sht_inverse_adjoint");
 }
 
@@ -666,41 +816,10 @@ sht_status sht_forward_adjoint(sht_plan_t p, const void *d_coeffs, void *d_sampl
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int L = p->L;
-    const int64_t Nc = 4 * batch;
-    double *X = p->ws.b, *W = p->ws.a, *U = p->ws.g;
-    cudaError_t e;
-    {
-        Span sp(p, SHT_STAGE_LAYOUT, s);
-        e = coeffs_to_orders(L, batch, (const double2 *)d_coeffs, X, s);
-    }
-    GemmArgs ga{};
-    ga.L = L; ga.batch = batch;
-    ga.part = p->ws.part; ga.part_cap = (int64_t)kSplitCap * L * Nc;
-    ga.launches = &p->launches;
-    // reverse of the forward chain: m = 0 .. L-1
-    for (int m = 0; m < L && e == cudaSuccess; ++m) {
-        const int n = L - m;
-        double *Xm = X + rows_off(L, m) * Nc;
-        if (m > 0) {
-            // adjoint of the alias subtraction: X_m -= Q_m^T U, U[k] = bins alias_k(+-m) of rings k < m
-            Span sp(p, SHT_STAGE_ALIAS, s);
-            e = gather_alias_bins(L, m, batch, W, U, s);
-            if (e == cudaSuccess)
-                e = gemm_f64(true, n, m, (int)Nc, p->pt + pt_off(L, m), n, U, Nc, Xm, Nc, EPI_SUB,
-                             ga, s, Xm);
-        }
-        if (e == cudaSuccess) {  // adjoint of the solve: bins +-m of rings k >= m = P_m^{-T} X_m
-            Span sp(p, SHT_STAGE_SOLVE, s);
-            e = gemm_f64(true, n, n, (int)Nc, p->pinv + pinv_off(L, m), n, Xm, Nc,
-                         W + rows_off(L, m) * Nc, Nc, EPI_STORE, ga, s);
-        }
-    }
-    if (e == cudaSuccess) {
-        Span sp(p, SHT_STAGE_RING_IDFT, s);
-        e = bins_to_ring_adjoint(L, p->dft, W, (double2 *)d_samples, batch, s);
-    }
-    p->launches += 1 + (L - 1) + ring_launches(L);  // layout, alias gathers, ring DFTs
+    const cudaError_t e =
+        p->dtype == SHT_F32
+            ? simt_forward_adjoint<float>(p, (const float2 *)d_coeffs, (float2 *)d_samples, batch, s)
+            : simt_forward_adjoint<double>(p, (const double2 *)d_coeffs, (double2 *)d_samples, batch, s);
     return cuda_check(e, "sht_forward_adjoint");
 }
 

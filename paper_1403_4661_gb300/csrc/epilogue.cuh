@@ -1,27 +1,29 @@
-// Epilogues shared by the float64 and the tensor-core contractions: one output row r and the four
-// columns c0..c0+3 of one signal, (+m re, +m im, -m re, -m im).
+// Epilogues shared by the float64 (and float32) and the tensor-core contractions: one output row r
+// and the four columns c0..c0+3 of one signal, (+m re, +m im, -m re, -m im).
 #pragma once
 
 #include "sht_internal.cuh"
 
 namespace sht {
 
-struct EpiArgs {
-    double *C; int64_t ldc;
-    const double *C0;   // EPI_SUB
+template <typename T>
+struct EpiArgsT {
+    T *C; int64_t ldc;
+    const T *C0;        // EPI_SUB
     int m, L, N;
-    double2 *coeffs;    // EPI_SOLVE
-    double *W;          // EPI_ALIAS
+    cplx_t<T> *coeffs;  // EPI_SOLVE
+    T *W;               // EPI_ALIAS
 };
+using EpiArgs = EpiArgsT<double>;
 
-template <int EPI>
-__device__ __forceinline__ void epilogue_row4(const EpiArgs &p, int r, int c0, const double v[4]) {
+template <int EPI, typename T>
+__device__ __forceinline__ void epilogue_row4(const EpiArgsT<T> &p, int r, int c0, const T v[4]) {
     const int m = p.m, N = p.N;
     if (EPI == EPI_STORE || EPI == EPI_SOLVE) {
-        double *cr = p.C + (int64_t)r * p.ldc + c0;
+        T *cr = p.C + (int64_t)r * p.ldc + c0;
         if (c0 + 4 <= N && (p.ldc & 1) == 0) {
-            *reinterpret_cast<double2 *>(cr) = make_double2(v[0], v[1]);
-            *reinterpret_cast<double2 *>(cr + 2) = make_double2(v[2], v[3]);
+            *reinterpret_cast<cplx_t<T> *>(cr) = mk2<T>(v[0], v[1]);
+            *reinterpret_cast<cplx_t<T> *>(cr + 2) = mk2<T>(v[2], v[3]);
         } else {
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -29,8 +31,8 @@ __device__ __forceinline__ void epilogue_row4(const EpiArgs &p, int r, int c0, c
         }
     }
     if (EPI == EPI_SUB) {
-        const double *c0r = p.C0 + (int64_t)r * p.ldc + c0;
-        double *cr = p.C + (int64_t)r * p.ldc + c0;
+        const T *c0r = p.C0 + (int64_t)r * p.ldc + c0;
+        T *cr = p.C + (int64_t)r * p.ldc + c0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) cr[j] = c0r[j] - v[j];
     }
@@ -38,11 +40,11 @@ __device__ __forceinline__ void epilogue_row4(const EpiArgs &p, int r, int c0, c
         // row r is degree l = m + r; columns (b, +m re/im, -m re/im)
         const int64_t L2 = (int64_t)p.L * p.L;
         const int l = m + r, b = c0 >> 2;
-        double2 *cb = p.coeffs + (int64_t)b * L2 + (int64_t)l * l + l;
-        cb[m] = make_double2(v[0], v[1]);
+        cplx_t<T> *cb = p.coeffs + (int64_t)b * L2 + (int64_t)l * l + l;
+        cb[m] = mk2<T>(v[0], v[1]);
         if (m > 0) {
-            const double sg = (m & 1) ? -1.0 : 1.0;   // f_l^{-m} = (-1)^m F_l^{-}
-            cb[-m] = make_double2(sg * v[2], sg * v[3]);
+            const T sg = (m & 1) ? (T)-1 : (T)1;   // f_l^{-m} = (-1)^m F_l^{-}
+            cb[-m] = mk2<T>(sg * v[2], sg * v[3]);
         }
     }
     if (EPI == EPI_ALIAS) {
@@ -50,7 +52,7 @@ __device__ __forceinline__ void epilogue_row4(const EpiArgs &p, int r, int c0, c
         const int k = r, b = c0 >> 2;
         const int a = alias_bin(m, k);
         const int o = a < 0 ? -a : a;
-        double *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
+        T *w = p.W + (rows_off(p.L, o) + (k - o)) * (int64_t)N + 4 * b;
         // read through L2 (__ldcg): in the persistent chain kernel other SMs updated these bins
         if (a == 0) {
             w[0] = __ldcg(w) - (v[0] + v[2]);

@@ -15,8 +15,9 @@ __device__ __forceinline__ void decode(int64_t idx, int &l, int &m) {
     m = (int)(idx - (int64_t)ll * ll - ll);
 }
 
-__global__ void k_coeffs_to_orders(int L, int64_t batch, const double2 *__restrict__ coeffs,
-                                   double *__restrict__ X) {
+template <typename T>
+__global__ void k_coeffs_to_orders(int L, int64_t batch, const cplx_t<T> *__restrict__ coeffs,
+                                   T *__restrict__ X) {
     const int64_t L2 = (int64_t)L * L;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L2 * batch) return;
@@ -24,19 +25,20 @@ __global__ void k_coeffs_to_orders(int L, int64_t batch, const double2 *__restri
     int l, m;
     decode(idx, l, m);
     const int o = m < 0 ? -m : m;
-    double *x = X + (rows_off(L, o) + (l - o)) * (4 * batch) + 4 * b;
-    double2 v = coeffs[t];
+    T *x = X + (rows_off(L, o) + (l - o)) * (4 * batch) + 4 * b;
+    cplx_t<T> v = coeffs[t];
     if (m >= 0) {
         x[0] = v.x; x[1] = v.y;
-        if (m == 0) { x[2] = 0.0; x[3] = 0.0; }
+        if (m == 0) { x[2] = 0; x[3] = 0; }
     } else {
-        const double sg = (o & 1) ? -1.0 : 1.0;
+        const T sg = (o & 1) ? (T)-1 : (T)1;
         x[2] = sg * v.x; x[3] = sg * v.y;
     }
 }
 
-__global__ void k_orders_to_coeffs(int L, int64_t batch, const double *__restrict__ X,
-                                   double2 *__restrict__ coeffs) {
+template <typename T>
+__global__ void k_orders_to_coeffs(int L, int64_t batch, const T *__restrict__ X,
+                                   cplx_t<T> *__restrict__ coeffs) {
     const int64_t L2 = (int64_t)L * L;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L2 * batch) return;
@@ -44,30 +46,37 @@ __global__ void k_orders_to_coeffs(int L, int64_t batch, const double *__restric
     int l, m;
     decode(idx, l, m);
     const int o = m < 0 ? -m : m;
-    const double *x = X + (rows_off(L, o) + (l - o)) * (4 * batch) + 4 * b;
+    const T *x = X + (rows_off(L, o) + (l - o)) * (4 * batch) + 4 * b;
     if (m >= 0) {
-        coeffs[t] = make_double2(x[0], x[1]);
+        coeffs[t] = mk2<T>(x[0], x[1]);
     } else {
-        const double sg = (o & 1) ? -1.0 : 1.0;
-        coeffs[t] = make_double2(sg * x[2], sg * x[3]);
+        const T sg = (o & 1) ? (T)-1 : (T)1;
+        coeffs[t] = mk2<T>(sg * x[2], sg * x[3]);
     }
 }
 
 // U[k][4b + 2s + c], k < m: bin alias_k(+m) (s = 0) and alias_k(-m) (s = 1) of ring k, read from
 // the order-major bins W (bin q of ring k: block |q|, row k - |q|, slot 0 for q >= 0, 2 for q < 0).
-__global__ void k_gather_alias_bins(int L, int m, int64_t batch, const double *__restrict__ W,
-                                    double *__restrict__ U) {
+template <typename T>
+__global__ void k_gather_alias_bins(int L, int m, int64_t batch, const T *__restrict__ W,
+                                    T *__restrict__ U) {
     const int64_t Nc = 4 * batch;
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)m * batch) return;
     const int k = (int)(t / batch), b = (int)(t - (int64_t)k * batch);
     const int a = alias_bin(m, k);
     const int o = a < 0 ? -a : a;
-    const double *w = W + (rows_off(L, o) + (k - o)) * Nc + 4 * b;
+    const T *w = W + (rows_off(L, o) + (k - o)) * Nc + 4 * b;
     const int sp = a >= 0 ? 0 : 2, sn = a > 0 ? 2 : 0;  // slots of bins a and -a (bin 0: slot 0)
-    double *u = U + (int64_t)k * Nc + 4 * b;
+    T *u = U + (int64_t)k * Nc + 4 * b;
     u[0] = w[sp]; u[1] = w[sp + 1];
     u[2] = w[sn]; u[3] = w[sn + 1];
+}
+
+// float64 -> float32 copy of a plan table (SHT_F32 plans)
+__global__ void k_to_f32(const double *__restrict__ in, float *__restrict__ out, int64_t n) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) out[t] = (float)in[t];
 }
 
 __global__ void k_residual(int64_t n, const double2 *__restrict__ s_in, double2 *__restrict__ r) {
@@ -117,22 +126,49 @@ cudaError_t update_with_max(int64_t n, double2 *x, const double2 *dx, double *mx
     return cudaGetLastError();
 }
 
-cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U, cudaStream_t s) {
+template <typename T>
+cudaError_t gather_alias_bins_t(int L, int m, int64_t batch, const T *W, T *U, cudaStream_t s) {
     int64_t n = (int64_t)m * batch;
     if (n <= 0) return cudaSuccess;
-    k_gather_alias_bins<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, m, batch, W, U);
+    k_gather_alias_bins<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, m, batch, W, U);
     return cudaGetLastError();
 }
+cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U, cudaStream_t s) {
+    return gather_alias_bins_t<double>(L, m, batch, W, U, s);
+}
+cudaError_t gather_alias_bins(int L, int m, int64_t batch, const float *W, float *U, cudaStream_t s) {
+    return gather_alias_bins_t<float>(L, m, batch, W, U, s);
+}
 
+template <typename T>
+cudaError_t coeffs_to_orders_t(int L, int64_t batch, const cplx_t<T> *coeffs, T *X, cudaStream_t s) {
+    int64_t n = (int64_t)L * L * batch;
+    k_coeffs_to_orders<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, coeffs, X);
+    return cudaGetLastError();
+}
 cudaError_t coeffs_to_orders(int L, int64_t batch, const double2 *coeffs, double *X, cudaStream_t s) {
-    int64_t n = (int64_t)L * L * batch;
-    k_coeffs_to_orders<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, coeffs, X);
-    return cudaGetLastError();
+    return coeffs_to_orders_t<double>(L, batch, coeffs, X, s);
+}
+cudaError_t coeffs_to_orders(int L, int64_t batch, const float2 *coeffs, float *X, cudaStream_t s) {
+    return coeffs_to_orders_t<float>(L, batch, coeffs, X, s);
 }
 
-cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coeffs, cudaStream_t s) {
+template <typename T>
+cudaError_t orders_to_coeffs_t(int L, int64_t batch, const T *X, cplx_t<T> *coeffs, cudaStream_t s) {
     int64_t n = (int64_t)L * L * batch;
-    k_orders_to_coeffs<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, X, coeffs);
+    k_orders_to_coeffs<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, X, coeffs);
+    return cudaGetLastError();
+}
+cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coeffs, cudaStream_t s) {
+    return orders_to_coeffs_t<double>(L, batch, X, coeffs, s);
+}
+cudaError_t orders_to_coeffs(int L, int64_t batch, const float *X, float2 *coeffs, cudaStream_t s) {
+    return orders_to_coeffs_t<float>(L, batch, X, coeffs, s);
+}
+
+cudaError_t table_to_f32(const double *in, float *out, int64_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
 }
 

@@ -58,6 +58,8 @@ extern "C" sht_status sht_forward_noalloc(sht_plan_t p, const void *d_samples, v
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
     if (dev != p->device) return set_error(SHT_ERR_INVALID_ARG, "current device is not the plan's device");
+    if (p->dtype == SHT_F32)
+        return set_error(SHT_ERR_UNSUPPORTED, "sht_forward_noalloc: complex128 plans only (not SHT_F32)");
     if (batch < 0 || batch > 65535) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [0, 65535]");
     if (batch == 0) return SHT_OK;
     if (!d_samples || !d_coeffs) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");

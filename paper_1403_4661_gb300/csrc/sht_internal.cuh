@@ -51,6 +51,19 @@ __host__ __device__ inline int alias_bin(int m, int k) {
     return r - k;
 }
 
+// Complex type of a real type (the float64 path and the float32 path of SHT_F32).
+template <typename T> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+template <typename T> using cplx_t = typename Cplx<T>::type;
+template <typename T>
+__host__ __device__ __forceinline__ cplx_t<T> mk2(T x, T y) {
+    cplx_t<T> r;
+    r.x = x;
+    r.y = y;
+    return r;
+}
+
 // Split-K partial buffer of the order chain holds this many L x 4B slices.
 constexpr int kSplitCap = 16;
 
@@ -64,6 +77,9 @@ struct DftPlan {
     int64_t *filt_off = nullptr;   // device, per ring (-1 for direct rings)
     int *filt_M = nullptr;         // device, per ring convolution length (0 for direct rings)
     double2 *twiddle = nullptr;    // e^{-2 pi i t / Mmax}, t < Mmax
+    int64_t filt_total = 0;        // complex values in filt
+    // SHT_F32 plans: the same tables rounded to float32 (dft_plan_make_f32)
+    float2 *chirp_f = nullptr, *filt_f = nullptr, *twiddle_f = nullptr;
     std::vector<int64_t> h_filt_off;
     std::vector<int> h_filt_M;
 };
@@ -94,6 +110,8 @@ struct sht_plan_s {
     double *d_theta = nullptr;
     double *pt = nullptr;       // P~ table
     double *pinv = nullptr;     // per-order inverses
+    float *ptF = nullptr;       // SHT_F32: the P~ table rounded to float32
+    float *pinvF = nullptr;     // SHT_F32: the per-order inverses rounded to float32
     sht::DftPlan dft;
     sht::Workspace ws;    // per-call scratch, grown to the largest batch seen
     double2 *stage = nullptr;     // uneven batches: gathered inputs, then outputs (stage_batch each)
@@ -160,6 +178,17 @@ cudaError_t bins_to_ring_adjoint(int L, const DftPlan &dp, const double *W, doub
 // adjoint of fold_ring_idft: samples -> unfolded synthesis table Gt
 cudaError_t ring_dft_unfold(int L, const DftPlan &dp, const double2 *samples, double *Gt,
                             int64_t batch, cudaStream_t s);
+// float32 tables of the ring DFTs (SHT_F32 plans), computed from the float64 ones
+cudaError_t dft_plan_make_f32(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s);
+// the same four transforms in float32 (complex64 samples, float order-major buffers)
+cudaError_t ring_dft_to_bins(int L, const DftPlan &dp, const float2 *samples, float *W,
+                             int64_t batch, bool scale, cudaStream_t s);
+cudaError_t fold_ring_idft(int L, const DftPlan &dp, const float *Gt, float2 *samples,
+                           int64_t batch, cudaStream_t s);
+cudaError_t bins_to_ring_adjoint(int L, const DftPlan &dp, const float *W, float2 *samples,
+                                 int64_t batch, cudaStream_t s);
+cudaError_t ring_dft_unfold(int L, const DftPlan &dp, const float2 *samples, float *Gt,
+                            int64_t batch, cudaStream_t s);
 
 // gemm_f64.cu
 enum Epilogue : int {
@@ -169,38 +198,53 @@ enum Epilogue : int {
     EPI_ADJ_SOLVE = 3,   // adjoint chain: W bins of order m (rows k >= m) = A^T B
     EPI_SUB = 4,         // C = C0 - A B (C0 given)
 };
-struct GemmArgs {
+template <typename T>
+struct GemmArgsT {
     int L;
     int64_t batch;
     int m;                 // order of this problem (single-problem launches)
-    double2 *coeffs;       // EPI_SOLVE output
-    double *W;             // EPI_ALIAS target
-    double *part = nullptr;  // split-K partial sums (none: no split)
-    int64_t part_cap = 0;    // doubles available at part
+    cplx_t<T> *coeffs;     // EPI_SOLVE output
+    T *W;                  // EPI_ALIAS target
+    T *part = nullptr;     // split-K partial sums (none: no split)
+    int64_t part_cap = 0;  // elements available at part
     int64_t *launches = nullptr;  // incremented by the number of kernels launched
 };
+using GemmArgs = GemmArgsT<double>;
 // Single problem: C[M x N] (+)= op(A)[M x K] * B[K x N], row-major, N = 4 * batch.
 cudaError_t gemm_f64(bool transA, int M, int K, int N, const double *A, int64_t lda,
                      const double *B, int64_t ldb, double *C, int64_t ldc, int epi,
                      const GemmArgs &ga, cudaStream_t s, const double *C0 = nullptr);
+// The same contraction in float32 (SHT_F32 plans), on the FP32 pipe.
+cudaError_t gemm_f32(bool transA, int M, int K, int N, const float *A, int64_t lda,
+                     const float *B, int64_t ldb, float *C, int64_t ldc, int epi,
+                     const GemmArgsT<float> &ga, cudaStream_t s, const float *C0 = nullptr);
 // Grouped over every order m: Gt[m][k][:] = P~[m][k][:] . X[m] (all k), or the transposed
 // contraction for the adjoint (out[m][l][:] = sum_k P~[m][k][l] U[m][k][:]).
 cudaError_t synthesis_all_orders(int L, int64_t batch, const double *pt, const double *X,
                                  double *Gt, cudaStream_t s);
 cudaError_t analysis_all_orders(int L, int64_t batch, const double *pt, const double *U,
                                 double *X, cudaStream_t s);
+cudaError_t synthesis_all_orders(int L, int64_t batch, const float *pt, const float *X,
+                                 float *Gt, cudaStream_t s);
+cudaError_t analysis_all_orders(int L, int64_t batch, const float *pt, const float *U,
+                                float *X, cudaStream_t s);
 
 // layout.cu: coefficient <-> order-major conversions
 cudaError_t coeffs_to_orders(int L, int64_t batch, const double2 *coeffs, double *X,
                              cudaStream_t s);
 cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coeffs,
                              cudaStream_t s);
+cudaError_t coeffs_to_orders(int L, int64_t batch, const float2 *coeffs, float *X, cudaStream_t s);
+cudaError_t orders_to_coeffs(int L, int64_t batch, const float *X, float2 *coeffs, cudaStream_t s);
+// n float64 values rounded to float32 (tables of SHT_F32 plans)
+cudaError_t table_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);
 // refinement: r = s - r (n complex values); x += dx and max |Re, Im dx| into *mx
 cudaError_t residual(int64_t n, const double2 *s_in, double2 *r, cudaStream_t s);
 cudaError_t update_with_max(int64_t n, double2 *x, const double2 *dx, double *mx, cudaStream_t s);
 // adjoint chain: U[k] (k < m) = the bins of ring k that orders +m / -m alias to
 cudaError_t gather_alias_bins(int L, int m, int64_t batch, const double *W, double *U,
                               cudaStream_t s);
+cudaError_t gather_alias_bins(int L, int m, int64_t batch, const float *W, float *U, cudaStream_t s);
 
 // tc_gemm.cu: float64-accurate contractions on the tensor cores from exact BF16 slices
 constexpr int kTcSlices = 8;     // slices per operand

@@ -26,8 +26,9 @@ SHT_F64_TENSOR = 1
 SHT_BF16_REFINED = 2
 SHT_BF16X2_REFINED = 3
 SHT_TF32_REFINED = 4
+SHT_F32 = 5
 DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR, "bf16_refined": SHT_BF16_REFINED,
-          "bf16x2_refined": SHT_BF16X2_REFINED, "tf32_refined": SHT_TF32_REFINED}
+          "bf16x2_refined": SHT_BF16X2_REFINED, "tf32_refined": SHT_TF32_REFINED, "f32": SHT_F32}
 SHT_ORDER_GREEDY = 0
 SHT_ORDER_SIMPLE = 1
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
@@ -178,18 +179,18 @@ def _call(name, h, inp, out, batch, stream=None):
               _stream_ptr(stream)))
 
 
-def _as_batch(x, L, name):
+def _as_batch(x, L, name, cdtype=torch.complex128):
     if not isinstance(x, torch.Tensor) or not x.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
-    if x.dtype != torch.complex128:
-        raise TypeError(f"{name} must be complex128")
+    if x.dtype != cdtype:
+        raise TypeError(f"{name} must be {str(cdtype).replace('torch.', '')} for this plan")
     if x.shape[-1] != L * L:
         raise ValueError(f"{name}: last dimension must be L^2 = {L * L}")
     return x.contiguous()
 
 
-def sht_forward(h, L, samples, out=None, stream=None):
-    x = _as_batch(samples, L, "samples")
+def sht_forward(h, L, samples, out=None, stream=None, cdtype=torch.complex128):
+    x = _as_batch(samples, L, "samples", cdtype)
     y = torch.empty_like(x) if out is None else out
     _call("sht_forward", h, x, y, x.numel() // (L * L), stream)
     return y
@@ -203,8 +204,8 @@ def sht_forward_noalloc(h, L, samples, out=None, stream=None):
     return y
 
 
-def sht_inverse(h, L, coeffs, out=None, stream=None):
-    x = _as_batch(coeffs, L, "coeffs")
+def sht_inverse(h, L, coeffs, out=None, stream=None, cdtype=torch.complex128):
+    x = _as_batch(coeffs, L, "coeffs", cdtype)
     y = torch.empty_like(x) if out is None else out
     _call("sht_inverse", h, x, y, x.numel() // (L * L), stream)
     return y
@@ -242,15 +243,15 @@ def inverse_uneven(plans, plan_index, offsets, coeffs, out=None, stream=None):
     return _uneven("sht_inverse_uneven", plans, plan_index, offsets, coeffs, out, stream)
 
 
-def sht_forward_adjoint(h, L, coeffs, out=None, stream=None):
-    x = _as_batch(coeffs, L, "coeffs")
+def sht_forward_adjoint(h, L, coeffs, out=None, stream=None, cdtype=torch.complex128):
+    x = _as_batch(coeffs, L, "coeffs", cdtype)
     y = torch.empty_like(x) if out is None else out
     _call("sht_forward_adjoint", h, x, y, x.numel() // (L * L), stream)
     return y
 
 
-def sht_inverse_adjoint(h, L, samples, out=None, stream=None):
-    x = _as_batch(samples, L, "samples")
+def sht_inverse_adjoint(h, L, samples, out=None, stream=None, cdtype=torch.complex128):
+    x = _as_batch(samples, L, "samples", cdtype)
     y = torch.empty_like(x) if out is None else out
     _call("sht_inverse_adjoint", h, x, y, x.numel() // (L * L), stream)
     return y
@@ -272,6 +273,8 @@ class Plan:
         self.L = int(L)
         dtype = DTYPES.get(dtype, dtype)
         self.dtype = dtype
+        # element type of the plan's signals: complex64 for SHT_F32, complex128 otherwise
+        self.cdtype = torch.complex64 if dtype == SHT_F32 else torch.complex128
         if theta is not None:
             self.handle = sht_plan_with_thetas(self.L, theta, dtype)
         else:
@@ -315,16 +318,16 @@ class Plan:
         return sht_plan_stage_times(self.handle)
 
     def forward(self, samples, out=None, stream=None):
-        return sht_forward(self.handle, self.L, samples, out, stream)
+        return sht_forward(self.handle, self.L, samples, out, stream, self.cdtype)
 
     def inverse(self, coeffs, out=None, stream=None):
-        return sht_inverse(self.handle, self.L, coeffs, out, stream)
+        return sht_inverse(self.handle, self.L, coeffs, out, stream, self.cdtype)
 
     def forward_adjoint(self, coeffs, out=None, stream=None):
-        return sht_forward_adjoint(self.handle, self.L, coeffs, out, stream)
+        return sht_forward_adjoint(self.handle, self.L, coeffs, out, stream, self.cdtype)
 
     def inverse_adjoint(self, samples, out=None, stream=None):
-        return sht_inverse_adjoint(self.handle, self.L, samples, out, stream)
+        return sht_inverse_adjoint(self.handle, self.L, samples, out, stream, self.cdtype)
 
 
 class SHTForward(torch.autograd.Function):
@@ -354,14 +357,15 @@ class SHTInverse(torch.autograd.Function):
 
 
 def forward(plan, samples):
-    """Differentiable forward SHT; real input is promoted to complex128."""
+    """Differentiable forward SHT; real input is promoted to the plan's complex type (complex128,
+    or complex64 for float32 plans)."""
     if not samples.is_complex():
-        samples = samples.to(torch.complex128)
+        samples = samples.to(plan.cdtype)
     return SHTForward.apply(plan, samples)
 
 
 def inverse(plan, coeffs):
     """Differentiable inverse SHT."""
     if not coeffs.is_complex():
-        coeffs = coeffs.to(torch.complex128)
+        coeffs = coeffs.to(plan.cdtype)
     return SHTInverse.apply(plan, coeffs)

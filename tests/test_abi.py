@@ -43,7 +43,8 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.sht_plan(0, 0, 0, ctypes.byref(h)) == 2          # SHT_ERR_UNSUPPORTED
     assert h.value is None
     assert lib.sht_plan(5000, 0, 0, ctypes.byref(h)) == 2
-    assert lib.sht_plan(8, 7, 0, ctypes.byref(h)) == 2           # unknown dtype
+    assert lib.sht_plan(8, 6, 0, ctypes.byref(h)) == 2           # unknown dtype
+    assert lib.sht_plan(8, -1, 0, ctypes.byref(h)) == 2
     assert lib.sht_plan(8, 0, 0, None) == 1                      # SHT_ERR_INVALID_ARG
     assert lib.sht_forward(None, None, None, 1, None) == 1       # NULL plan
     assert lib.sht_status_string(4) == b"SHT_ERR_CUDA"
