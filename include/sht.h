@@ -226,6 +226,49 @@ sht_status sht_forward_noalloc(sht_plan_t plan, const void *d_samples, void *d_c
 sht_status sht_plan_set_refinement(sht_plan_t plan, int max_iters, double tol);
 
 /*
+ * Execution choices of a plan for one batch size (a project addition; the paper has no
+ * counterpart: it fixes the method's arithmetic, not how a GPU schedules it).
+ *   forward_path, inverse_path: SHT_PATH_DEFAULT (the plan's arithmetic: tensor-core kernels for
+ *     SHT_F64_TENSOR and the refined plans, SIMT kernels for SHT_F64 and SHT_F32),
+ *     SHT_PATH_TENSOR, or SHT_PATH_SIMT (the float64 SIMT kernels on the plan's float64 tables;
+ *     offered to SHT_F64_TENSOR plans for both directions and to refined plans for the inverse;
+ *     float64-accurate like the tensor path).
+ *   split_cap: most K-splits of one per-order product of the SIMT order chain (0 = default 16,
+ *     else 1..16).
+ *   forward_ms, inverse_ms: the times sht_plan_autotune measured for the chosen paths (0 when set
+ *     by sht_plan_set_paths).
+ */
+#define SHT_PATH_DEFAULT 0
+#define SHT_PATH_TENSOR  1
+#define SHT_PATH_SIMT    2
+typedef struct {
+    int forward_path;
+    int inverse_path;
+    int split_cap;
+    double forward_ms;
+    double inverse_ms;
+} sht_tuning;
+
+/*
+ * sht_plan_set_paths - use these choices for later calls whose batch equals `batch` (other
+ *   batches keep the defaults).  SHT_ERR_INVALID_ARG for a path the plan does not offer or a
+ *   split_cap outside 0..16.
+ */
+sht_status sht_plan_set_paths(sht_plan_t plan, int64_t batch, int forward_path, int inverse_path,
+                              int split_cap);
+
+/*
+ * sht_plan_autotune - time every choice the plan offers for batches of `batch` signals (forward:
+ *   the tensor chain where offered, the SIMT chain with split caps 16, 4 and 1; inverse: the
+ *   tensor synthesis where offered and the SIMT synthesis), each as the best of three calls after
+ *   one warm-up on zero-filled device buffers of its own, keep the fastest for later calls with
+ *   that batch, and report it in *out (may be NULL).  Refined plans tune their inverse only.
+ *   Blocking; allocates and frees its buffers and the plan's workspaces grow to `batch`; do not
+ *   call it while a stream is being captured.
+ */
+sht_status sht_plan_autotune(sht_plan_t plan, int64_t batch, sht_tuning *out);
+
+/*
  * sht_plan_set_wait_limit - limit, in seconds (1e-9 .. 60), of every wait inside the tensor-core
  *   kernels of the plan on other CTAs or on its own copy and MMA pipeline (grid barriers of the
  *   forward chain, mbarriers).  A wait that reaches the limit abandons the call: its CTA sets the

@@ -290,6 +290,12 @@ sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch
     return SHT_OK;
 }
 
+// The execution choices recorded for this batch size (sht_plan_set_paths / sht_plan_autotune).
+const sht_tuning *tuning_for(sht_plan_t p, int64_t batch) {
+    auto it = p->tuned.find(batch);
+    return it == p->tuned.end() ? nullptr : &it->second;
+}
+
 // SIMT contractions of the float64 (T = double) and float32 (T = float) plans: tables and GEMM.
 template <typename T> const T *pt_table(sht_plan_t p);
 template <> const double *pt_table<double>(sht_plan_t p) { return p->pt; }
@@ -321,6 +327,7 @@ cudaError_t simt_chain(sht_plan_t p, Workspace &w, T *W, cplx_t<T> *d_coeffs, in
     ga.L = L; ga.batch = batch; ga.coeffs = d_coeffs; ga.W = W;
     ga.part = reinterpret_cast<T *>(w.part); ga.part_cap = (int64_t)kSplitCap * L * Nc;
     ga.launches = &p->launches;
+    if (const sht_tuning *t = tuning_for(p, batch)) ga.split_cap = t->split_cap;
     for (int m = L - 1; m >= 0 && e == cudaSuccess; --m) {
         const int n = L - m;
         ga.m = m;
@@ -454,7 +461,9 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         e = ring_dft_to_bins(L, p->dft, d_samples, W, batch, true, s);
     }
     p->launches += ring_launches(L);
-    if (tensor_plan(p)) {
+    const sht_tuning *tu = tuning_for(p, batch);
+    const bool simt = !tensor_plan(p) || (nsl == kTcSlices && tu && tu->forward_path == SHT_PATH_SIMT);
+    if (!simt) {
         // Eqs. (14)-(16) for every order in one persistent launch (stage span: solve)
         Span sp(p, SHT_STAGE_SOLVE, s);
         const bool tf32 = p->refine_tf32 && nsl < kTcSlices;   // the TF32 refinement's F_lo
@@ -473,7 +482,9 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
 // Inverse transform (Procedure 2), float64-accurate for every plan arithmetic but SHT_F32.
 cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, double2 *d_samples,
                          int64_t batch, cudaStream_t s) {
-    if (!tensor_plan(p)) return simt_inverse<double>(p, w, d_coeffs, d_samples, batch, s);
+    const sht_tuning *tu = tuning_for(p, batch);
+    if (!tensor_plan(p) || (tu && tu->inverse_path == SHT_PATH_SIMT))
+        return simt_inverse<double>(p, w, d_coeffs, d_samples, batch, s);
     const int L = p->L;
     cudaError_t e;
     {
@@ -719,6 +730,107 @@ sht_status sht_plan_set_refinement(sht_plan_t p, int max_iters, double tol) {
     p->refine_max_iters = max_iters;
     p->refine_tol = tol;
     return SHT_OK;
+}
+
+sht_status sht_plan_set_paths(sht_plan_t p, int64_t batch, int forward_path, int inverse_path, int split_cap) {
+    sht_status st = check_plan(p);
+    if (st != SHT_OK) return st;
+    if (batch < 1 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [1, 65535]");
+    if (split_cap < 0 || split_cap > 16) return set_error(SHT_ERR_INVALID_ARG, "split_cap outside 0..16");
+    const bool tensor = tensor_plan(p), refined = p->refine_nsl > 0;
+    auto offered = [&](int path, bool fwd) {
+        if (path == SHT_PATH_DEFAULT) return true;
+        if (path == SHT_PATH_TENSOR) return tensor;
+        if (path == SHT_PATH_SIMT) return !(fwd && refined);
+        return false;
+    };
+    if (!offered(forward_path, true) || !offered(inverse_path, false))
+        return set_error(SHT_ERR_INVALID_ARG, "execution path not offered by this plan's arithmetic");
+    sht_tuning t{};
+    t.forward_path = forward_path;
+    t.inverse_path = inverse_path;
+    t.split_cap = split_cap;
+    p->tuned[batch] = t;
+    return SHT_OK;
+}
+
+sht_status sht_plan_autotune(sht_plan_t p, int64_t batch, sht_tuning *out) {
+    sht_status st = check_plan(p);
+    if (st != SHT_OK) return st;
+    if (batch < 1 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [1, 65535]");
+    if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
+    const bool tensor = tensor_plan(p), refined = p->refine_nsl > 0;
+    const size_t bytes = (size_t)elem_bytes(p) * (size_t)p->L * (size_t)p->L * (size_t)batch;
+    void *in = nullptr, *outb = nullptr;
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&in, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&outb, bytes);
+    if (e == cudaSuccess) e = cudaMemset(in, 0, bytes);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    // best of three timed calls after one warm-up, with `cand` recorded for this batch
+    auto time_call = [&](bool fwd, const sht_tuning &cand, double &ms) -> sht_status {
+        p->tuned[batch] = cand;
+        ms = INFINITY;
+        for (int r = 0; r < 4; ++r) {
+            cudaEventRecord(e0, s);
+            sht_status cs = fwd ? sht_forward(p, in, outb, batch, s) : sht_inverse(p, in, outb, batch, s);
+            if (cs != SHT_OK) return cs;
+            cudaEventRecord(e1, s);
+            cudaError_t ce = cudaEventSynchronize(e1);
+            float t = 0.f;
+            if (ce == cudaSuccess) ce = cudaEventElapsedTime(&t, e0, e1);
+            if (ce != cudaSuccess) return cuda_check(ce, "sht_plan_autotune timing");
+            if (r > 0) ms = std::min(ms, (double)t);
+        }
+        return SHT_OK;
+    };
+    sht_tuning best{};
+    if (e != cudaSuccess) {
+        st = cuda_check(e, "sht_plan_autotune buffers");
+    } else {
+        std::vector<sht_tuning> fwd, inv;
+        sht_tuning c{};
+        if (refined) {
+            fwd.push_back(c);   // the refinement keeps its forward
+        } else {
+            if (tensor) { c.forward_path = SHT_PATH_TENSOR; fwd.push_back(c); }
+            for (int cap : {16, 4, 1}) { c.forward_path = SHT_PATH_SIMT; c.split_cap = cap; fwd.push_back(c); }
+        }
+        c = sht_tuning{};
+        if (tensor) { c.inverse_path = SHT_PATH_TENSOR; inv.push_back(c); }
+        c.inverse_path = SHT_PATH_SIMT;
+        inv.push_back(c);
+        double bf = INFINITY, bi = INFINITY;
+        for (const sht_tuning &cand : fwd) {
+            if (refined) break;
+            double ms = 0;
+            if ((st = time_call(true, cand, ms)) != SHT_OK) break;
+            if (ms < bf) { bf = ms; best.forward_path = cand.forward_path; best.split_cap = cand.split_cap; }
+        }
+        for (size_t i = 0; i < inv.size() && st == SHT_OK; ++i) {
+            sht_tuning cand = inv[i];
+            cand.forward_path = best.forward_path;
+            cand.split_cap = best.split_cap;
+            double ms = 0;
+            if ((st = time_call(false, cand, ms)) != SHT_OK) break;
+            if (ms < bi) { bi = ms; best.inverse_path = cand.inverse_path; }
+        }
+        best.forward_ms = refined ? 0.0 : bf;
+        best.inverse_ms = bi;
+    }
+    if (st == SHT_OK) p->tuned[batch] = best;
+    else p->tuned.erase(batch);
+    if (s) cudaStreamSynchronize(s);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (s) cudaStreamDestroy(s);
+    cudaFree(in);
+    cudaFree(outb);
+    if (st == SHT_OK && out) *out = best;
+    return st;
 }
 
 sht_status sht_plan_check(sht_plan_t p) {

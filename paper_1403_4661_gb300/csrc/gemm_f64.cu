@@ -204,7 +204,9 @@ cudaError_t launch_cfg(const Params<T> &p, Cfg c, dim3 grid, cudaStream_t s) {
 int64_t tiles_of(int M, int N, Cfg c) { return cdiv(M, c.bm) * cdiv(N, c.bn); }
 
 template <typename T, bool TA, int EPI>
-cudaError_t launch_single(Params<T> p, cudaStream_t s, T *part, int64_t part_cap, int64_t *count) {
+cudaError_t launch_single(Params<T> p, cudaStream_t s, T *part, int64_t part_cap, int64_t *count,
+                          int split_cap) {
+    const int cap = split_cap > 0 ? std::min(split_cap, kMaxSplit) : kMaxSplit;
     Cfg c{64, 64};
     if (p.N <= 32) {
         c = Cfg{16, 16};
@@ -217,7 +219,7 @@ cudaError_t launch_single(Params<T> p, cudaStream_t s, T *part, int64_t part_cap
     const int64_t tiles = tiles_of(p.M, p.N, c);
     int splits = 1;
     if (part && tiles < 2 * kSMs && p.K >= 128) {
-        splits = (int)std::min<int64_t>(std::min<int64_t>(cdiv(2 * kSMs, tiles), p.K / 64), kMaxSplit);
+        splits = (int)std::min<int64_t>(std::min<int64_t>(cdiv(2 * kSMs, tiles), p.K / 64), cap);
         while (splits > 1 && (int64_t)splits * p.M * p.N > part_cap) --splits;
     }
     if (count) *count += splits <= 1 ? 1 : 2;
@@ -241,8 +243,8 @@ cudaError_t gemm_t(bool transA, int M, int K, int N, const T *A, int64_t lda, co
     p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc; p.C0 = C0;
     p.M = M; p.K = K; p.N = N; p.m = ga.m; p.L = ga.L; p.coeffs = ga.coeffs; p.W = ga.W;
 #define SHT_GEMM_CASE(E)                                                                        \
-    if (epi == E) return transA ? launch_single<T, true, E>(p, s, ga.part, ga.part_cap, ga.launches) \
-                                : launch_single<T, false, E>(p, s, ga.part, ga.part_cap, ga.launches);
+    if (epi == E) return transA ? launch_single<T, true, E>(p, s, ga.part, ga.part_cap, ga.launches, ga.split_cap) \
+                                : launch_single<T, false, E>(p, s, ga.part, ga.part_cap, ga.launches, ga.split_cap);
     SHT_GEMM_CASE(EPI_STORE)
     SHT_GEMM_CASE(EPI_SOLVE)
     SHT_GEMM_CASE(EPI_ALIAS)

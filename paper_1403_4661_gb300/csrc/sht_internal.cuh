@@ -24,6 +24,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -143,6 +144,8 @@ struct sht_plan_s {
     int refine_iters = 0;
     double refine_last = 0.0;
     double *d_refine_max = nullptr;
+    // execution choices per batch size (sht_plan_set_paths, sht_plan_autotune)
+    std::map<int64_t, sht_tuning> tuned;
     // stage timing (sht_plan_set_timing)
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -207,6 +210,7 @@ struct GemmArgsT {
     T *W;                  // EPI_ALIAS target
     T *part = nullptr;     // split-K partial sums (none: no split)
     int64_t part_cap = 0;  // elements available at part
+    int split_cap = 0;     // most K-splits per product (0: the launcher's default, 16)
     int64_t *launches = nullptr;  // incremented by the number of kernels launched
 };
 using GemmArgs = GemmArgsT<double>;

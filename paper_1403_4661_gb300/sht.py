@@ -36,7 +36,12 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
             "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement",
-            "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit"]
+            "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit",
+            "sht_plan_set_paths", "sht_plan_autotune"]
+SHT_PATH_DEFAULT = 0
+SHT_PATH_TENSOR = 1
+SHT_PATH_SIMT = 2
+PATHS = {"default": SHT_PATH_DEFAULT, "tensor": SHT_PATH_TENSOR, "simt": SHT_PATH_SIMT}
 STAGES = ["ring_dft", "solve", "alias", "layout", "synthesis", "ring_idft"]
 
 
@@ -52,6 +57,11 @@ class ShtInfo(ctypes.Structure):
                 ("plan_seconds", ctypes.c_double), ("order_seconds", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("refine_iterations", ctypes.c_int),
                 ("refine_last_update", ctypes.c_double)]
+
+
+class ShtTuning(ctypes.Structure):
+    _fields_ = [("forward_path", ctypes.c_int), ("inverse_path", ctypes.c_int), ("split_cap", ctypes.c_int),
+                ("forward_ms", ctypes.c_double), ("inverse_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -88,6 +98,8 @@ def load_library(path=LIB_PATH):
     for name in ("sht_forward_uneven", "sht_inverse_uneven"):
         getattr(lib, name).argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i64), P, P, P]
+    lib.sht_plan_set_paths.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.sht_plan_autotune.argtypes = [P, i64, ctypes.POINTER(ShtTuning)]
     lib.sht_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.sht_plan_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
     lib.sht_last_error_message.argtypes = []
@@ -302,6 +314,20 @@ class Plan:
     def set_refinement(self, max_iters=10, tol=1e-11):
         """Iteration control of refined plans (tol = 0: fixed iterations, no synchronisation)."""
         sht_plan_set_refinement(self.handle, max_iters, tol)
+
+    def set_paths(self, batch, forward="default", inverse="default", split_cap=0):
+        """Pin the execution paths used for calls with this batch size (sht_plan_set_paths)."""
+        _check(load_library().sht_plan_set_paths(self.handle, int(batch), PATHS.get(forward, forward),
+                                                 PATHS.get(inverse, inverse), int(split_cap)))
+
+    def autotune(self, batch):
+        """Time every execution path the plan offers at this batch size and keep the fastest
+        (sht_plan_autotune); returns the choice and its measured times."""
+        t = ShtTuning()
+        _check(load_library().sht_plan_autotune(self.handle, int(batch), ctypes.byref(t)))
+        names = {v: k for k, v in PATHS.items()}
+        return {"forward_path": names[t.forward_path], "inverse_path": names[t.inverse_path],
+                "split_cap": t.split_cap, "forward_ms": t.forward_ms, "inverse_ms": t.inverse_ms}
 
     def set_wait_limit(self, seconds=1.0):
         """Limit of the tensor kernels' waits on other CTAs and on their pipeline."""
