@@ -197,21 +197,6 @@ __device__ __forceinline__ void sum_partials(const ChainArgs &p, const Partials 
     for (int q = 0; q < 4; ++q) v[q] = i64_scaled(t[q], er + scale_from_field(__ldcg(pa.sc.fB + c0 + q)));
 }
 
-// The alias subtraction from one bin group of a ring (signal b's 4 columns (+q re, +q im, -q re,
-// -q im) of the row that holds bin a): v = (G_{+m} re, im, G_{-m} re, im), as in EPI_ALIAS.
-__device__ __forceinline__ void alias_update(double w[4], int a, const double v[4]) {
-    if (a == 0) {
-        w[0] -= v[0] + v[2];
-        w[1] -= v[1] + v[3];
-    } else {
-        const int sp = a > 0 ? 0 : 2, sm = 2 - sp;
-        w[sp] -= v[0];
-        w[sp + 1] -= v[1];
-        w[sm] -= v[2];
-        w[sm + 1] -= v[3];
-    }
-}
-
 // The contraction's items (output tile, K-split), one per CTA and round; each stores its int64
 // partial.  `ok` turns false (for the whole CTA) when an mbarrier wait gives up.
 // NSL BF16 slices per operand (kind::f16), or, with TF, one TF32 value per operand (kind::tf32:
@@ -314,7 +299,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             }
             if (jb.first && kbase == 0 && h == 0) x[0] = s_row0[j];   // row 0: g_m's completed first row
             const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
-            if (TF) {
+            if constexpr (TF) {
                 // canonical K-major layout of 32-bit elements: core matrices of 8 columns x 4 K
                 // (16 bytes per column), NT * 16 bytes apart along K; rows kk, kk + 1 side by side
 #pragma unroll
@@ -325,21 +310,21 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                                  "r"(tf32_scaled_bits(x[2 * q + 1], e))
                                  : "memory");
                 }
-                return;
-            }
+            } else {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int kk = 2 * (h + 4 * q);
-                __nv_bfloat16 lo[S], hi[S];
-                split_value(x[2 * q], e, lo);
-                split_value(x[2 * q + 1], e, hi);
-                const uint32_t a = cb + (kk >> 3) * (NT * 16) + (kk & 7) * 2;
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = 2 * (h + 4 * q);
+                    __nv_bfloat16 lo[S], hi[S];
+                    split_value(x[2 * q], e, lo);
+                    split_value(x[2 * q + 1], e, hi);
+                    const uint32_t a = cb + (kk >> 3) * (NT * 16) + (kk & 7) * 2;
 #pragma unroll
-                for (int s = 0; s < NSL; ++s)
-                    asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a + s * (NT * KB * 2)),
-                                 "r"((uint32_t)__bfloat16_as_ushort(lo[s]) |
-                                     ((uint32_t)__bfloat16_as_ushort(hi[s]) << 16))
-                                 : "memory");
+                    for (int s = 0; s < NSL; ++s)
+                        asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a + s * (NT * KB * 2)),
+                                     "r"((uint32_t)__bfloat16_as_ushort(lo[s]) |
+                                         ((uint32_t)__bfloat16_as_ushort(hi[s]) << 16))
+                                     : "memory");
+                }
             }
         };
 

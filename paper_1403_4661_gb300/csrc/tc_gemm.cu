@@ -111,14 +111,6 @@ __device__ __forceinline__ void slice_cols_block(const double *__restrict__ X, i
     }
 }
 
-// One warp per column (the order chain's per-step operands: few columns, many warps).
-__global__ void k_slice_cols(const double *__restrict__ X, int64_t ld, int K, int cols, int kp,
-                             __nv_bfloat16 *__restrict__ out, int64_t sstride, int *__restrict__ expo) {
-    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= cols) return;
-    slice_row_warp(X + j, ld, K, kp, out + (int64_t)j * kp, sstride, expo + j);
-}
-
 // Order-major coefficients X (block m: L - m rows of Nc columns), every order m = blockIdx.y.
 __global__ void k_slice_cols_orders(const double *__restrict__ X, int L, int Nc,
                                     const int64_t *__restrict__ koff, __nv_bfloat16 *__restrict__ out,

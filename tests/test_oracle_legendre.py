@@ -49,6 +49,11 @@ def test_matches_scipy_up_to_l100():
         for l in range(m, L, 3):
             ref = sph_harm_y(l, m, THETA, 0.0).real
             np.testing.assert_allclose(got[:, l - m], ref, rtol=1e-10, atol=1e-13)
+        # negative orders through Eq. (23), against scipy's own Y_l^{-m} (not the symmetry)
+        gotn = ptilde_signed(-m, L, THETA, bases)
+        for l in range(m, L, 7):
+            ref = sph_harm_y(l, -m, THETA, 0.0).real
+            np.testing.assert_allclose(gotn[:, l - m], ref, rtol=1e-10, atol=1e-13)
 
 
 def test_extended_range_against_mpmath():
