@@ -299,7 +299,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             }
             if (jb.first && kbase == 0 && h == 0) x[0] = s_row0[j];   // row 0: g_m's completed first row
             const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
-            if constexpr (TF) {
+            if (TF) {
                 // canonical K-major layout of 32-bit elements: core matrices of 8 columns x 4 K
                 // (16 bytes per column), NT * 16 bytes apart along K; rows kk, kk + 1 side by side
 #pragma unroll
@@ -310,21 +310,21 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                                  "r"(tf32_scaled_bits(x[2 * q + 1], e))
                                  : "memory");
                 }
-            } else {
+                return;
+            }
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int kk = 2 * (h + 4 * q);
-                    __nv_bfloat16 lo[S], hi[S];
-                    split_value(x[2 * q], e, lo);
-                    split_value(x[2 * q + 1], e, hi);
-                    const uint32_t a = cb + (kk >> 3) * (NT * 16) + (kk & 7) * 2;
+            for (int q = 0; q < 4; ++q) {
+                const int kk = 2 * (h + 4 * q);
+                __nv_bfloat16 lo[S], hi[S];
+                split_value(x[2 * q], e, lo);
+                split_value(x[2 * q + 1], e, hi);
+                const uint32_t a = cb + (kk >> 3) * (NT * 16) + (kk & 7) * 2;
 #pragma unroll
-                    for (int s = 0; s < NSL; ++s)
-                        asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a + s * (NT * KB * 2)),
-                                     "r"((uint32_t)__bfloat16_as_ushort(lo[s]) |
-                                         ((uint32_t)__bfloat16_as_ushort(hi[s]) << 16))
-                                     : "memory");
-                }
+                for (int s = 0; s < NSL; ++s)
+                    asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a + s * (NT * KB * 2)),
+                                 "r"((uint32_t)__bfloat16_as_ushort(lo[s]) |
+                                     ((uint32_t)__bfloat16_as_ushort(hi[s]) << 16))
+                                 : "memory");
             }
         };
 
