@@ -119,6 +119,20 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out);
 sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host, uint32_t flags,
                                 sht_plan_t *out);
 
+/*
+ * sht_plan_save, sht_plan_load - keep a plan's ring co-latitudes on disk, so that a later process
+ *   skips the greedy ordering (Sec. III-E; O(L^4), 23 s at L = 1024 on GB300) and rebuilds only the
+ *   tables.  The paper stores the co-latitudes once per L for the same reason (Sec. III-E).
+ *   File (little-endian): the 8 bytes "SHTTHETA", int32 L, int32 0, L float64 co-latitudes in
+ *   ring order, then the 64-bit FNV-1a hash of all preceding bytes.
+ *   sht_plan_save writes the file at `path` (host data only, no device work); SHT_ERR_INVALID_ARG
+ *   if it cannot be written.  sht_plan_load reads and checks it (size, tag, L in 1..SHT_MAX_L,
+ *   hash; SHT_ERR_INVALID_ARG on any mismatch, before any device work), then builds a plan of
+ *   arithmetic `dtype` exactly as sht_plan_with_thetas does.
+ */
+sht_status sht_plan_save(sht_plan_t plan, const char *path);
+sht_status sht_plan_load(const char *path, sht_dtype dtype, sht_plan_t *out);
+
 /* sht_plan_thetas - copy the plan's L ring co-latitudes to theta_host_out (host, L doubles). */
 sht_status sht_plan_thetas(sht_plan_t plan, double *theta_host_out);
 

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 
@@ -676,6 +677,58 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     std::vector<double> th(L);
     for (int k = 0; k < L; ++k) th[k] = M_PI * (2.0 * order[k] + 1.0) / (2.0 * L - 1.0);
     return build_plan(L, dtype, th, order_s, out);
+}
+
+// 64-bit FNV-1a over a byte range (the file hash of sht_plan_save / sht_plan_load).
+static uint64_t fnv1a64(const unsigned char *b, size_t n, uint64_t h = 0xcbf29ce484222325ull) {
+    for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 0x100000001b3ull; }
+    return h;
+}
+static const char kThetaTag[8] = {'S', 'H', 'T', 'T', 'H', 'E', 'T', 'A'};
+
+sht_status sht_plan_save(sht_plan_t p, const char *path) {
+    if (!p || !path) return set_error(SHT_ERR_INVALID_ARG, "NULL argument");
+    std::vector<unsigned char> buf(16 + 8 * (size_t)p->L);
+    std::memcpy(buf.data(), kThetaTag, 8);
+    const int32_t hdr[2] = {p->L, 0};
+    std::memcpy(buf.data() + 8, hdr, 8);
+    std::memcpy(buf.data() + 16, p->theta.data(), 8 * (size_t)p->L);
+    const uint64_t h = fnv1a64(buf.data(), buf.size());
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return set_error(SHT_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    const bool ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size() && std::fwrite(&h, 8, 1, f) == 1;
+    const bool closed = std::fclose(f) == 0;
+    if (!ok || !closed) return set_error(SHT_ERR_INVALID_ARG, std::string("cannot write ") + path);
+    return SHT_OK;
+}
+
+sht_status sht_plan_load(const char *path, sht_dtype dtype, sht_plan_t *out) {
+    if (!out || !path) return set_error(SHT_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return set_error(SHT_ERR_INVALID_ARG, std::string("cannot open ") + path);
+    std::vector<unsigned char> buf;
+    unsigned char chunk[4096];
+    size_t n;
+    while ((n = std::fread(chunk, 1, sizeof(chunk), f)) > 0 && buf.size() <= 16 + 8 * (size_t)kMaxL + 8)
+        buf.insert(buf.end(), chunk, chunk + n);
+    std::fclose(f);
+    if (buf.size() < 24 || std::memcmp(buf.data(), kThetaTag, 8) != 0)
+        return set_error(SHT_ERR_INVALID_ARG, "not a co-latitude file (tag)");
+    int32_t hdr[2];
+    std::memcpy(hdr, buf.data() + 8, 8);
+    const int L = hdr[0];
+    if (L < 1 || L > kMaxL || hdr[1] != 0)
+        return set_error(SHT_ERR_INVALID_ARG, "co-latitude file: L outside [1, 2048] or bad header");
+    if (buf.size() != 16 + 8 * (size_t)L + 8)
+        return set_error(SHT_ERR_INVALID_ARG, "co-latitude file: size does not match L");
+    uint64_t h;
+    std::memcpy(&h, buf.data() + 16 + 8 * (size_t)L, 8);
+    if (h != fnv1a64(buf.data(), 16 + 8 * (size_t)L))
+        return set_error(SHT_ERR_INVALID_ARG, "co-latitude file: hash mismatch");
+    std::vector<double> th((size_t)L);
+    std::memcpy(th.data(), buf.data() + 16, 8 * (size_t)L);
+    return sht_plan_with_thetas(L, dtype, th.data(), 0u, out);
 }
 
 sht_status sht_plan_thetas(sht_plan_t p, double *theta_host_out) {

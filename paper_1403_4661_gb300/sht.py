@@ -37,7 +37,7 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
             "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement",
             "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit",
-            "sht_plan_set_paths", "sht_plan_autotune"]
+            "sht_plan_set_paths", "sht_plan_autotune", "sht_plan_save", "sht_plan_load"]
 SHT_PATH_DEFAULT = 0
 SHT_PATH_TENSOR = 1
 SHT_PATH_SIMT = 2
@@ -99,6 +99,8 @@ def load_library(path=LIB_PATH):
         getattr(lib, name).argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i64), P, P, P]
     lib.sht_plan_set_paths.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.sht_plan_save.argtypes = [P, ctypes.c_char_p]
+    lib.sht_plan_load.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(P)]
     lib.sht_plan_autotune.argtypes = [P, i64, ctypes.POINTER(ShtTuning)]
     lib.sht_plan_set_timing.argtypes = [P, ctypes.c_int]
     lib.sht_plan_stage_times.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -293,6 +295,24 @@ class Plan:
             flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering]
             self.handle = sht_plan(self.L, dtype, flags)
         self.theta = sht_plan_thetas(self.handle, self.L)
+
+    @classmethod
+    def load(cls, path, dtype=SHT_F64):
+        """A plan on the co-latitudes stored by Plan.save (sht_plan_load): no ring ordering."""
+        dtype = DTYPES.get(dtype, dtype)
+        h = ctypes.c_void_p()
+        _check(load_library().sht_plan_load(os.fsencode(path), int(dtype), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self.handle = h
+        self.L = load_library().sht_plan_bandlimit(h)
+        self.dtype = dtype
+        self.cdtype = torch.complex64 if dtype == SHT_F32 else torch.complex128
+        self.theta = sht_plan_thetas(h, self.L)
+        return self
+
+    def save(self, path):
+        """Store the plan's ring co-latitudes in a checksummed file (sht_plan_save)."""
+        _check(load_library().sht_plan_save(self.handle, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "handle", None) is not None:
