@@ -424,7 +424,7 @@ def run_ours(args):
         roof = {"bound": "alu",
                 "kernel": "k_gemm<64,64,4,0,0,1,0> (float64 synthesis, Eq. (11))",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "GB300 float64 pipe, 1.25 TFLOP/s at 2070 MHz (DESIGN.md); at the measured "
+                "peak_source": "GB300 float64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flops, 1.25 TFLOP/s at 2070 MHz; at the measured "
                                f"median {sm_mhz:.0f} MHz the clock-scaled peak is {peak * sm_mhz / FP64_NOMINAL_MHZ:.3f}",
                 "traffic": _traffic_record("synthesis_f64", L, B)}
     roof["stage_ms_per_step"] = {k: v[0] / stage_steps for k, v in stages.items()}

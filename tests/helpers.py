@@ -23,5 +23,6 @@ def oracle_thetas(L):
 
 
 def tol_samples(s):
-    """1e-11 relative to the signal's largest sample (inverse outputs)."""
+    """1e-11 relative to the signal's largest sample: an inverse output sums up to 2 L^2 terms of
+    size up to |P~| ~ sqrt(2L / 4 pi), and the oracle's own float64 error is of that order."""
     return 1e-11 * max(1.0, float(np.abs(s).max()))
