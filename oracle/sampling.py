@@ -16,6 +16,14 @@ Two orderings of Theta into theta are given:
 Reading: "condition number" is the 2-norm one, sigma_max / sigma_min (the paper's wording "ratio of
 the largest eigenvalue to the smallest" is not defined for a non-symmetric P_m); exact ties go to
 the lowest index t.
+
+Sec. III-F (alternative placement): the sets Theta^1 and Theta^2 put the L rings at equal steps of
+the measures sin(theta) d theta and |tan(theta)|^(1/3) d theta, starting from Theta_0 = pi (the
+south pole): the measure between consecutive elements is 1/L of its integral over [0, pi]
+(2/L and 2 pi/(L sqrt 3)).  Here they are built literally from that definition (numerical
+integration, root finding) and sorted ascending like Eq. (19), so that the same index orderings
+(Eq. (20) or condition-number minimisation) turn them into theta^1, theta^2.  The ring kept
+farthest from the poles is the element nearest pi/2 (for Eq. (19) that is index floor((L-1)/2)).
 """
 import math
 
@@ -48,6 +56,76 @@ def equiangular_set(L):
     return math.pi * (2.0 * t + 1.0) / (2.0 * L - 1.0)
 
 
+def _cumulative_measure(measure):
+    """C(x) = measure of [x, pi] for the placement measures of Sec. III-F."""
+    from scipy import integrate
+
+    if measure == "sin":
+        return lambda x: integrate.quad(math.sin, x, math.pi, epsabs=1e-13, epsrel=1e-13)[0]
+    if measure != "tan13":
+        raise ValueError(measure)
+    # F(x) = integral of |tan t|^(1/3) over [0, x].  For x <= pi/2 the substitutions u = tan t,
+    # w = u^(1/3) turn it into the integral of 3 w^3 / (1 + w^6) over [0, W], W = tan(x)^(1/3); the
+    # part beyond w = 1, with v = 1/w, is the integral of 3 v / (1 + v^6) over [1/W, 1].  Both
+    # integrands are smooth on [0, 1].  |tan| is symmetric about pi/2: F(x) = 2 F(pi/2) - F(pi - x).
+    f = lambda w: 3.0 * w ** 3 / (1.0 + w ** 6)   # noqa: E731
+    f_inv = lambda v: 3.0 * v / (1.0 + v ** 6)    # noqa: E731
+    q = lambda fn, a, b: integrate.quad(fn, a, b, epsabs=1e-14, epsrel=1e-13)[0]   # noqa: E731
+    half = q(f, 0.0, 1.0) + q(f_inv, 0.0, 1.0)
+
+    def F_left(x):
+        W = math.tan(x) ** (1.0 / 3.0) if x < math.pi / 2 else np.inf
+        if W <= 1.0:
+            return q(f, 0.0, W)
+        return half - q(f_inv, 0.0, 1.0 / W)
+
+    def F(x):
+        return F_left(x) if x <= math.pi / 2 else 2.0 * half - F_left(math.pi - x)
+
+    return lambda x: 2.0 * half - F(x)
+
+
+def measure_set(L, measure="uniform"):
+    """The ring set of a placement rule, ascending: "uniform" is Eq. (19); "sin" and "tan13" are
+    Theta^1 and Theta^2 of Sec. III-F: Theta_0 = pi and, for t = 1..L-1, the measure of
+    [Theta_t, Theta_{t-1}] equal to 1/L of the measure of [0, pi], i.e. C(Theta_t) = t C(0) / L
+    with C(x) the measure of [x, pi]."""
+    if measure == "uniform":
+        return equiangular_set(L)
+    from scipy import optimize
+
+    C = _cumulative_measure(measure)
+    step = C(0.0) / L
+    out = [math.pi]
+    for t in range(1, L):
+        out.append(optimize.brentq(lambda x: C(x) - t * step, 0.0, out[-1], xtol=1e-15, rtol=1e-15))
+    return np.sort(np.array(out))
+
+
+def middle_index(Theta):
+    """Index of the element of Theta nearest pi/2; mirror pairs (equal distance up to rounding,
+    within 1e-12) go to the lowest index."""
+    d = np.abs(np.asarray(Theta) - math.pi / 2)
+    return int(np.nonzero(d <= d.min() + 1e-12)[0][0])
+
+
+# Reading for the mirror-symmetric sets Theta^1, Theta^2: reflecting a ring about pi/2 multiplies
+# its row of P_m by (-1)^(l+m) column by column, an orthogonal change that leaves the condition
+# number unchanged whenever the fixed rows are themselves symmetric, so mirror candidates tie
+# exactly in exact arithmetic and rounding would break the tie arbitrarily.  For those sets the
+# greedy takes the lowest index among candidates within a relative 1e-9 of the smallest condition
+# number.  Eq. (19) has no mirror pairs (pi - Theta_t is never in it); its rule stays exact ties.
+TIE_RTOL = {"uniform": 0.0, "sin": 1e-9, "tan13": 1e-9}
+
+
+def _pick(cand, kappa, rtol):
+    kappa = np.asarray(kappa, dtype=np.float64)
+    if rtol == 0.0:
+        return cand[int(np.argmin(kappa))]
+    kmin = kappa.min()
+    return cand[int(np.nonzero(kappa <= kmin * (1.0 + rtol))[0][0])] if np.isfinite(kmin) else cand[0]
+
+
 def simple_order(L):
     """Indices t into Theta for the ordering of Eq. (20): [L-1, 0, L-2, 1, L-3, 2, ...]."""
     order = [L - 1]
@@ -77,28 +155,23 @@ def cond_exact(P):
     return s[0] / s[-1]
 
 
-def greedy_order_exact(L):
-    """Condition-number-minimisation ordering (Sec. III-E), every candidate scored by a full SVD.
+def greedy_order_exact(L, measure="uniform"):
+    """Condition-number-minimisation ordering (Sec. III-E), every candidate scored by a full SVD,
+    on the ring set of `measure` (measure_set).
 
-    Returns the indices t into Theta for theta_0..theta_{L-1}.  O(L^5); meant for L <= ~64.
+    Returns the indices t into the set for theta_0..theta_{L-1}.  O(L^5); meant for L <= ~64.
     """
-    Theta = equiangular_set(L)
+    Theta = measure_set(L, measure)
     order = np.full(L, -1, dtype=np.int64)
-    order[L - 1] = (L - 1) // 2
+    order[L - 1] = (L - 1) // 2 if measure == "uniform" else middle_index(Theta)
     used = {order[L - 1]}
     for m in range(L - 2, -1, -1):
         # the full table P~_l^m(Theta_t), l = m..L-1, for every t
         T = _order_block(m, L, Theta)
         fixed = T[order[m + 1:]]
-        best_t, best_k = -1, np.inf
-        for t in range(L):
-            if t in used:
-                continue
-            k = cond_exact(np.vstack([T[t][None, :], fixed]))
-            if k < best_k:
-                best_t, best_k = t, k
-        if best_t < 0:  # every candidate singular: take the lowest unused index
-            best_t = min(set(range(L)) - used)
+        cand = np.array([t for t in range(L) if t not in used], dtype=np.int64)
+        kappa = [cond_exact(np.vstack([T[t][None, :], fixed])) for t in cand]
+        best_t = _pick(cand, kappa, TIE_RTOL[measure])   # all singular: the lowest unused index
         order[m] = best_t
         used.add(best_t)
     return order
@@ -123,7 +196,7 @@ def _bisect_secular(mu, z2, lo, hi, iters=200):
     return 0.5 * (lo + hi)
 
 
-def greedy_order_secular(L):
+def greedy_order_secular(L, measure="uniform"):
     """Same ordering as ``greedy_order_exact``, with each candidate scored through the rank-one
     update of the fixed block's Gram matrix (O(L^4) overall).
 
@@ -133,9 +206,9 @@ def greedy_order_secular(L):
     interlacing the smallest lies in [mu_0, mu_1] and the largest in [mu_max, mu_max + |r|^2].
     kappa = sqrt(largest / smallest).
     """
-    Theta = equiangular_set(L)
+    Theta = measure_set(L, measure)
     order = np.full(L, -1, dtype=np.int64)
-    order[L - 1] = (L - 1) // 2
+    order[L - 1] = (L - 1) // 2 if measure == "uniform" else middle_index(Theta)
     used = np.zeros(L, dtype=bool)
     used[order[L - 1]] = True
     bases = sectoral_bases(L, Theta)
@@ -161,21 +234,22 @@ def greedy_order_secular(L):
             lam_max = _bisect_secular(mu, Z2, np.full(cand.size, mu[-1]), mu[-1] + r2)
         with np.errstate(divide="ignore", invalid="ignore"):
             kappa = np.where(lam_min > 0.0, np.sqrt(lam_max / lam_min), np.inf)
-        pick = cand[int(np.argmin(kappa))]
+        pick = _pick(cand, kappa, TIE_RTOL[measure])
         order[m] = pick
         used[pick] = True
     return order
 
 
-def thetas(L, ordering="greedy"):
-    """The ordered co-latitude vector theta (Eq. (7)) for an ordering rule."""
-    Theta = equiangular_set(L)
+def thetas(L, ordering="greedy", measure="uniform"):
+    """The ordered co-latitude vector theta (Eq. (7)) for an ordering rule, on the ring set of a
+    placement measure (Eq. (19) by default; Theta^1, Theta^2 of Sec. III-F)."""
+    Theta = measure_set(L, measure)
     if ordering == "simple":
         return Theta[simple_order(L)]
     if ordering == "greedy":
-        return Theta[greedy_order_secular(L)]
+        return Theta[greedy_order_secular(L, measure)]
     if ordering == "greedy_exact":
-        return Theta[greedy_order_exact(L)]
+        return Theta[greedy_order_exact(L, measure)]
     raise ValueError(ordering)
 
 

@@ -73,3 +73,75 @@ def test_golden_orders_are_permutations():
         o = np.loadtxt(path, dtype=np.int64, comments="#")
         assert sorted(o.tolist()) == list(range(L))
         assert o[L - 1] == (L - 1) // 2 and o[0] == L - 1
+
+
+def _tan13_integral(x):
+    """Integral of |tan t|^(1/3) over [0, x], x in [0, pi], in closed form (an independent method
+    from the oracle's numerical integration): with T = tan(x)^(2/3) and t = tan^(2/3), the
+    integrand becomes (3/2) T / (1 + T^3) dT, whose partial fractions -1/(3(1+T)) +
+    (T+1)/(3(T^2-T+1)) integrate to h(T) below; |tan| is symmetric about pi/2."""
+    half = math.pi / math.sqrt(3.0)
+
+    def left(y):
+        if y >= math.pi / 2:
+            return half
+        T = math.tan(y) ** (2.0 / 3.0)
+        h = (-math.log1p(T) / 3.0 + math.log(T * T - T + 1.0) / 6.0
+             + (math.atan((2.0 * T - 1.0) / math.sqrt(3.0)) + math.pi / 6.0) / math.sqrt(3.0))
+        return 1.5 * h
+
+    return left(x) if x <= math.pi / 2 else 2.0 * half - left(math.pi - x)
+
+
+@pytest.mark.parametrize("L", [8, 17, 32])
+def test_alternative_measure_sets_pinned(L):
+    """Theta^1 (sin measure) against its closed form cos Theta_t = 2t/L - 1; Theta^2 (|tan|^(1/3)
+    measure) against the closed-form integral: the measure of [Theta_t, pi] is t/L of the total
+    2 pi/sqrt(3); both start at the south pole and are mirror-symmetric about pi/2 apart from it."""
+    T1 = sampling.measure_set(L, "sin")
+    np.testing.assert_allclose(T1, np.sort(np.arccos(2.0 * np.arange(L) / L - 1.0)), atol=1e-13, rtol=0)
+    T2 = sampling.measure_set(L, "tan13")
+    total = 2.0 * math.pi / math.sqrt(3.0)
+    for t, x in enumerate(T2[::-1]):          # Theta_0 = pi first
+        if t == 0:
+            continue   # Theta_0 = pi by definition (asserted below); the measure is flat there
+        # the angle whose closed-form measure of [angle, pi] is t/L of the total, by bisection
+        # (compared as angles: next to pi/2 the measure changes steeply with the angle)
+        lo, hi = 0.0, math.pi
+        for _ in range(200):
+            mid = 0.5 * (lo + hi)
+            if total - _tan13_integral(mid) > total * t / L:
+                lo = mid
+            else:
+                hi = mid
+        assert abs(x - 0.5 * (lo + hi)) < 1e-13, t
+    for T in (T1, T2):
+        assert T[-1] == math.pi
+        u = T[:-1]
+        np.testing.assert_allclose(u + u[::-1], math.pi, atol=1e-13, rtol=0)
+    np.testing.assert_array_equal(sampling.measure_set(L, "uniform"), sampling.equiangular_set(L))
+
+
+@pytest.mark.parametrize("L", [6, 9, 12, 16])
+@pytest.mark.parametrize("measure", ["sin", "tan13"])
+def test_greedy_fast_equals_exact_on_alternative_sets(L, measure):
+    np.testing.assert_array_equal(sampling.greedy_order_secular(L, measure),
+                                  sampling.greedy_order_exact(L, measure))
+
+
+def test_kappa_study_of_alternative_measures():
+    """Sec. III-F: rings placed by the measures sin(theta) d theta and |tan(theta)|^(1/3) d theta
+    make the P_m far worse conditioned than the equiangular set, and condition-number minimisation
+    does not rescue them (the paper shows this in figures only; the values are this code's)."""
+    L = 32
+    k = {(ms, od): sampling.order_conditions(L, sampling.thetas(L, od, ms)).max()
+         for ms in ("uniform", "sin", "tan13") for od in ("simple", "greedy")}
+    expect = {("uniform", "simple"): 39.3565, ("uniform", "greedy"): 7.61121,
+              ("sin", "simple"): 2.64023e9, ("sin", "greedy"): 2.64023e9,
+              ("tan13", "simple"): 3.78515e11, ("tan13", "greedy"): 3.78515e11}
+    for key, v in expect.items():
+        assert abs(k[key] - v) <= 1e-3 * v, (key, k[key])
+    for ms in ("sin", "tan13"):
+        assert k[ms, "greedy"] > 1e8 * k["uniform", "greedy"]
+        assert k[ms, "greedy"] > 0.5 * k[ms, "simple"]      # reordering does not help
+    assert k["uniform", "greedy"] < k["uniform", "simple"] / 5  # it does for Eq. (19)
