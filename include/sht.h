@@ -97,12 +97,22 @@ typedef enum {
 #define SHT_ORDER_SIMPLE 1u   /* Eq. (20): pi, then alternately north / south to the equator   */
 #define SHT_ORDER_MASK   1u
 
+/* Plan flags: the set the rings are drawn from (Sec. III-E, III-F), ordered by the rule above. */
+#define SHT_MEASURE_UNIFORM 0u   /* Eq. (19): Theta_t = pi (2t+1)/(2L-1)                          */
+#define SHT_MEASURE_SIN     2u   /* Theta^1: from the south pole, equal steps of sin(theta) dtheta */
+#define SHT_MEASURE_TAN13   4u   /* Theta^2: equal steps of |tan(theta)|^(1/3) dtheta              */
+#define SHT_MEASURE_MASK    6u
+
 #define SHT_MAX_L 2048   /* longest ring 4095: its chirp-z length 8192 fits one SM */
 
 /*
  * sht_plan - build a plan for band-limit L (1 <= L <= SHT_MAX_L); batch is at most 65535.
- *   Ring co-latitudes come from the equiangular set Theta_t = pi (2t+1)/(2L-1) (Eq. (19)),
- *   ordered by the rule in `flags` (Sec. III-E).  The greedy ordering scores every candidate ring
+ *   Ring co-latitudes come from the equiangular set Theta_t = pi (2t+1)/(2L-1) (Eq. (19)), or
+ *   from the sets Theta^1, Theta^2 of the alternative measures (Sec. III-F, SHT_MEASURE_* flags;
+ *   the paper shows they make P_m far worse conditioned), ordered by the rule in `flags`
+ *   (Sec. III-E).  The ring kept farthest from the poles is the element nearest pi/2; on the
+ *   mirror-symmetric sets Theta^1, Theta^2 candidates within a relative 1e-9 of the smallest
+ *   condition number count as ties (lowest index wins).  The greedy ordering scores every candidate ring
  *   by the exact 2-norm condition number of P_m (Eq. (12)) through the eigen-decomposition of the
  *   fixed rows' Gram matrix and a rank-one secular equation; it costs O(L^4) and runs on the GPU.
  *   Then builds, on the current device: the P~_l^m(theta_k) table for all m >= 0, k, l >= m

@@ -623,6 +623,61 @@ sht_status uneven(bool forward, const sht_plan_t *plans, int nplans, int64_t nsi
     return SHT_OK;
 }
 
+// Integral of |tan t|^(1/3) over [0, x], x in [0, pi], in closed form: with T = tan(x)^(2/3) the
+// integrand becomes (3/2) T / (1 + T^3) dT, whose partial fractions -1/(3(1+T)) + (T+1)/(3(T^2-T+1))
+// integrate to h(T) below; |tan| is symmetric about pi/2 and the integral over [0, pi/2] is
+// pi / sqrt(3).
+static double tan13_half(double y) {
+    const double s3 = std::sqrt(3.0);
+    if (y >= M_PI / 2) return M_PI / s3;
+    const double T = std::pow(std::tan(y), 2.0 / 3.0);
+    const double h = -std::log1p(T) / 3.0 + std::log(T * T - T + 1.0) / 6.0 +
+                     (std::atan((2.0 * T - 1.0) / s3) + M_PI / 6.0) / s3;
+    return 1.5 * h;
+}
+static double tan13_integral(double x) {
+    return x <= M_PI / 2 ? tan13_half(x) : 2.0 * M_PI / std::sqrt(3.0) - tan13_half(M_PI - x);
+}
+
+// The ascending ring set of a placement measure.  SHT_MEASURE_UNIFORM: Eq. (19).  The sets of
+// Sec. III-F start at Theta_0 = pi and put 1/L of the measure between consecutive elements, so the
+// measure of [Theta_t, pi] is t/L of the total: 1 + cos(Theta_t) = 2t/L for sin(theta) dtheta, and
+// for |tan(theta)|^(1/3) dtheta Theta_t solves the closed-form integral by bisection.
+std::vector<double> ring_set(int L, uint32_t measure) {
+    std::vector<double> T((size_t)L);
+    if (measure == SHT_MEASURE_UNIFORM) {
+        for (int t = 0; t < L; ++t) T[t] = M_PI * (2.0 * t + 1.0) / (2.0 * L - 1.0);
+        return T;
+    }
+    const double total = 2.0 * M_PI / std::sqrt(3.0);
+    T[0] = M_PI;
+    for (int t = 1; t < L; ++t) {
+        if (measure == SHT_MEASURE_SIN) {
+            T[t] = std::acos(2.0 * t / L - 1.0);
+        } else {
+            const double target = total * (1.0 - (double)t / L);   // integral over [0, Theta_t]
+            double lo = 0.0, hi = M_PI;
+            for (int it = 0; it < 200 && hi - lo > 0.0; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (mid <= lo || mid >= hi) break;
+                (tan13_integral(mid) < target ? lo : hi) = mid;
+            }
+            T[t] = 0.5 * (lo + hi);
+        }
+    }
+    std::sort(T.begin(), T.end());
+    return T;
+}
+
+// Index of the element nearest pi/2 (mirror pairs, equal within 1e-12, to the lowest index).
+int middle_index(const std::vector<double> &T) {
+    double dmin = INFINITY;
+    for (double v : T) dmin = std::min(dmin, std::fabs(v - M_PI / 2));
+    for (size_t i = 0; i < T.size(); ++i)
+        if (std::fabs(T[i] - M_PI / 2) <= dmin + 1e-12) return (int)i;
+    return 0;
+}
+
 }  // namespace
 
 extern "C" {
@@ -662,6 +717,10 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
     if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    const uint32_t measure = flags & SHT_MEASURE_MASK;
+    if (measure != SHT_MEASURE_UNIFORM && measure != SHT_MEASURE_SIN && measure != SHT_MEASURE_TAN13)
+        return set_error(SHT_ERR_INVALID_ARG, "unknown ring measure in flags");
+    const std::vector<double> Theta = ring_set(L, measure);
     std::vector<int> order(L);
     auto t0 = std::chrono::steady_clock::now();
     if ((flags & SHT_ORDER_MASK) == SHT_ORDER_SIMPLE) {
@@ -670,12 +729,14 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
         int lo = 0, hi = L - 2;
         for (int k = 1; k < L; ++k) order[k] = (k & 1) ? lo++ : hi--;
     } else {
-        sht_status st = greedy_order(L, order);
+        const bool uniform = measure == SHT_MEASURE_UNIFORM;
+        sht_status st = greedy_order(L, Theta, uniform ? (L - 1) / 2 : middle_index(Theta),
+                                     uniform ? 0.0 : 1e-9, order);
         if (st != SHT_OK) return st;
     }
     double order_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     std::vector<double> th(L);
-    for (int k = 0; k < L; ++k) th[k] = M_PI * (2.0 * order[k] + 1.0) / (2.0 * L - 1.0);
+    for (int k = 0; k < L; ++k) th[k] = Theta[order[k]];
     return build_plan(L, dtype, th, order_s, out);
 }
 

@@ -1,9 +1,9 @@
 // Ring ordering by condition-number minimisation (Sec. III-E), on the GPU, plan time only.
 //
-// theta_{L-1} is the ring of the equiangular set (Eq. (19)) farthest from the poles; then for
-// m = L-2, ..., 0, theta_m is the unused ring minimising the 2-norm condition number of P_m
-// (Eq. (12)) whose other rows theta_{m+1..L-1} are already fixed.  Exact ties go to the lowest
-// index of the equiangular set.
+// theta_{L-1} is the ring of the set (Eq. (19), or a set of Sec. III-F) farthest from the poles;
+// then for m = L-2, ..., 0, theta_m is the unused ring minimising the 2-norm condition number of
+// P_m (Eq. (12)) whose other rows theta_{m+1..L-1} are already fixed.  Exact ties go to the lowest
+// index of the set (within a relative tolerance on the mirror-symmetric sets of Sec. III-F).
 //
 // Scoring every candidate at once: with B the fixed (n-1) x n block and r a candidate row,
 // P_m^T P_m = B^T B + r r^T.  From one eigen-decomposition B^T B = V diag(mu) V^T per order
@@ -83,15 +83,14 @@ struct Scratch {
 
 }  // namespace
 
-sht_status greedy_order(int L, std::vector<int> &order) {
+sht_status greedy_order(int L, const std::vector<double> &Theta, int middle, double tie_rtol,
+                        std::vector<int> &order) {
     order.assign(L, -1);
-    order[L - 1] = (L - 1) / 2;
+    order[L - 1] = middle;
     if (L <= 2) {
         if (L == 2) order[0] = 1 - order[1];
         return SHT_OK;
     }
-    std::vector<double> Theta(L);
-    for (int t = 0; t < L; ++t) Theta[t] = M_PI * (2.0 * t + 1.0) / (2.0 * L - 1.0);
 
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
@@ -167,6 +166,9 @@ sht_status greedy_order(int L, std::vector<int> &order) {
                 int best = 0;
                 for (int c = 1; c < nc; ++c)
                     if (kap[c] < kap[best]) best = c;
+                if (tie_rtol > 0.0)   // the lowest index within the tolerance of the smallest
+                    for (int c = 0; c < best; ++c)
+                        if (kap[c] <= kap[best] * (1.0 + tie_rtol)) { best = c; break; }
                 order[m] = cand[best];
                 used[cand[best]] = 1;
             }

@@ -302,7 +302,10 @@ cudaError_t tc_synthesis_all_orders(int L, int64_t batch, const int *ptE, const 
                                     const int *xE, const unsigned char *tmB, double *Gt, int *status,
                                     uint64_t wait_ns, cudaStream_t s);
 
-// planner.cu: greedy condition-number ordering (indices into the equiangular set)
-sht_status greedy_order(int L, std::vector<int> &order);
+// planner.cu: greedy condition-number ordering (indices into the ascending ring set Theta);
+// candidates within a relative tie_rtol of the smallest condition number go to the lowest index
+// (0: exact ties only); `middle` is the index of the ring kept farthest from the poles.
+sht_status greedy_order(int L, const std::vector<double> &Theta, int middle, double tie_rtol,
+                        std::vector<int> &order);
 
 }  // namespace sht

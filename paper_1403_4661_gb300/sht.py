@@ -31,6 +31,7 @@ DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR, "bf16_refined": SHT_BF16
           "bf16x2_refined": SHT_BF16X2_REFINED, "tf32_refined": SHT_TF32_REFINED, "f32": SHT_F32}
 SHT_ORDER_GREEDY = 0
 SHT_ORDER_SIMPLE = 1
+MEASURES = {"uniform": 0, "sin": 2, "tan13": 4}   # SHT_MEASURE_* flags
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
             "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
@@ -280,10 +281,11 @@ class Plan:
 
     Plan(L)                           greedy condition-number ring ordering (Sec. III-E)
     Plan(L, ordering="simple")        the ordering of Eq. (20)
+    Plan(L, measure="sin" | "tan13")  rings from the sets of the alternative measures (Sec. III-F)
     Plan(L, theta=array_of_L_values)  caller-given ring co-latitudes
     """
 
-    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64):
+    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64, measure="uniform"):
         self.L = int(L)
         dtype = DTYPES.get(dtype, dtype)
         self.dtype = dtype
@@ -292,7 +294,7 @@ class Plan:
         if theta is not None:
             self.handle = sht_plan_with_thetas(self.L, theta, dtype)
         else:
-            flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering]
+            flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering] | MEASURES[measure]
             self.handle = sht_plan(self.L, dtype, flags)
         self.theta = sht_plan_thetas(self.handle, self.L)
 

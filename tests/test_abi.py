@@ -46,6 +46,7 @@ def test_host_argument_checks_without_gpu(lib):
     assert lib.sht_plan(8, 6, 0, ctypes.byref(h)) == 2           # unknown dtype
     assert lib.sht_plan(8, -1, 0, ctypes.byref(h)) == 2
     assert lib.sht_plan(8, 0, 0, None) == 1                      # SHT_ERR_INVALID_ARG
+    assert lib.sht_plan(8, 0, 6, ctypes.byref(h)) == 1           # both ring-measure bits
     assert lib.sht_forward(None, None, None, 1, None) == 1       # NULL plan
     assert lib.sht_plan_set_paths(None, 1, 0, 0, 0) == 1
     assert lib.sht_plan_autotune(None, 1, None) == 1
