@@ -156,10 +156,12 @@ def _oracle_sample(L, seed, frac):
 
 
 def _host_cores():
+    """Cores this process may run on (at most 64 oracle processes: ~0.2 GB each at L = 1024)."""
     try:
-        return len(os.sched_getaffinity(0))
+        n = len(os.sched_getaffinity(0))
     except AttributeError:
-        return os.cpu_count() or 1
+        n = os.cpu_count() or 1
+    return max(1, min(n, 64))
 
 
 def _cpu_baseline_parallel(L, frac, steps, procs):
