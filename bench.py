@@ -13,9 +13,9 @@ exact slices (--dtype f64 for the float64 pipe).  Inputs (1 GiB per buffer) are 
 Under torchrun (N > 1) every rank transforms its own batch (weak scaling, no collective on the
 data path); the time is the max over ranks.
 
---impl reference times the plain float64 CPU oracle on this host (rank 0 only): each step is a
-bounded sample of the same workload - one signal, the last 1/16 of the orders of Procedure 2's
-loop and the first 1/16 of the iterations of Procedure 1's loop - scaled to signals/s.
+--impl reference times the plain float64 CPU oracle on this host (rank 0 only): each step runs,
+in one process per host core, a bounded sample of the same workload - 1/16 of the orders of
+Procedure 2's and Procedure 1's loops, spread evenly over m - counted as 1/16 of a signal each.
 """
 import argparse
 import json
@@ -49,18 +49,6 @@ def _peaks():
 # FFMA64 microbenchmark recorded in profiles/fp64_peak.md reproduces); scaled by the measured clock.
 FP64_TFLOPS_NOMINAL = 1.25
 FP64_NOMINAL_MHZ = 2070.0
-
-
-def _traffic_record(kernel, L, batch):
-    """DRAM bytes per launch from the committed ncu summary, if it covers this kernel/workload."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
-        return None
-    for line in open(path):
-        parts = dict(p.split("=", 1) for p in line.split() if "=" in p)
-        if parts.get("kernel") == kernel and parts.get("L") == str(L) and parts.get("batch") == str(batch):
-            return float(parts["dram_bytes_per_launch"])
-    return None
 
 
 class ClockSampler:
@@ -139,19 +127,30 @@ def _whole_job_rate(world_size, batch_per_rank, ms_per_step):
     return world_size * batch_per_rank / (ms_per_step * 1e-3)
 
 
-def _oracle_sample(L, seed, frac):
-    """One bounded oracle sample: returns seconds for 1/frac of each procedure's order loop."""
+def _oracle_order(L):
+    """The oracle's greedy ring ordering: the stored file (written by
+    tests/golden/make_ring_orders.py) when there is one, else computed."""
+    from oracle import sampling
+    path = os.path.join(ROOT, "tests", "golden", f"ring_order_L{L}.txt")
+    if os.path.exists(path):
+        return np.loadtxt(path, dtype=np.int64, comments="#")
+    return sampling.greedy_order_secular(L)
+
+
+def _oracle_sample(L, seed, frac, residue=0):
+    """One bounded oracle sample: seconds for the iterations m = residue (mod frac) of each
+    procedure's order loop, i.e. 1/frac of the orders spread evenly over 0..L-1 (so the sample
+    has the cost profile of the whole loop)."""
     from oracle import sht as osht
     from oracle import sampling
     from paper_1403_4661_gb300 import synth
-    from tests.helpers import oracle_order
 
-    theta = sampling.equiangular_set(L)[oracle_order(L)]
+    theta = sampling.equiangular_set(L)[_oracle_order(L)]
     c = synth.decaying_coeffs(L, 1, seed)
-    m_lo = L - L // frac
+    orders = range(residue % frac, L, frac)
     t0 = time.perf_counter()
-    s = osht.inverse(c, L, theta, m_lo=m_lo)
-    osht.forward(s, L, theta, m_lo=m_lo)
+    s = osht.inverse(c, L, theta, orders=orders)
+    osht.forward(s, L, theta, orders=orders)
     return time.perf_counter() - t0
 
 
@@ -170,10 +169,10 @@ def _cpu_baseline_parallel(L, frac, steps, procs):
     Returns, per step, the slowest process's seconds (the processes run concurrently, so `procs`
     samples complete in that time)."""
     code = ("import sys, json; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps([bench._oracle_sample(%d, 100 + i + 1000 * %d, %d) for i in range(%d)]))")
+            "print(json.dumps([bench._oracle_sample(%d, 100 + i + 1000 * %d, %d, %d + i) for i in range(%d)]))")
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    ps = [subprocess.Popen([sys.executable, "-c", code % (ROOT, L, p, frac, steps)], stdout=subprocess.PIPE,
+    ps = [subprocess.Popen([sys.executable, "-c", code % (ROOT, L, p, frac, p, steps)], stdout=subprocess.PIPE,
                            stderr=subprocess.PIPE, text=True, env=env, cwd=ROOT) for p in range(procs)]
     outs = [p.communicate() for p in ps]
     for p, (_, err) in zip(ps, outs):
@@ -185,9 +184,9 @@ def _cpu_baseline_parallel(L, frac, steps, procs):
 
 def _sample_text(L, procs):
     return (f"{procs} signals at L={L}, one per host core in {procs} concurrent single-threaded "
-            f"processes; each the last 1/{SAMPLE_FRACTION} of Procedure 2's order loop and the first "
-            f"1/{SAMPLE_FRACTION} of Procedure 1's, x{SAMPLE_FRACTION} (the sampled orders are the cheap "
-            "ones: measured at L=512, the full run takes 1.5x the scaled 1/8 sample)")
+            f"processes; each runs the iterations m = r (mod {SAMPLE_FRACTION}) of Procedure 2's and "
+            f"Procedure 1's order loops (1/{SAMPLE_FRACTION} of the orders, spread evenly over 0..L-1; "
+            f"r differs per process and step), counted as 1/{SAMPLE_FRACTION} of a signal")
 
 
 def run_reference(args):
@@ -196,15 +195,22 @@ def run_reference(args):
         return
     procs = _host_cores()
     times = _cpu_baseline_parallel(args.L, SAMPLE_FRACTION, args.warmup + args.steps, procs)[args.warmup:]
-    per_signal = statistics.mean(times) * SAMPLE_FRACTION / procs
-    value = 1.0 / per_signal
+    # a step runs `procs` bounded samples at once, each 1/SAMPLE_FRACTION of one signal's work
+    step_s = statistics.mean(times)
+    value = procs / (SAMPLE_FRACTION * step_s)
     sample = _sample_text(args.L, procs)
+    cfg = _config(args)
+    cfg["arithmetic"] = "f64 (plain float64 numpy oracle on the host CPU)"
+    cfg["workload"] = (f"{args.batch} complex signals at L={args.L}, f_lm re/im iid N(0,1)/(l+1); inverse SHT "
+                       "then forward SHT by the oracle's Procedures 2 and 1 (plain float64, host CPU); "
+                       "timed on a bounded sample, see cpu_baseline.sample")
+    cfg["launch"] = "host processes, one per core"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "signals/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * per_signal * args.batch, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": 1e3 * step_s, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(args),
+        "config": cfg,
         "cpu_baseline": {"value": value, "unit": "signals/s", "cores": procs, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "signals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -392,63 +398,18 @@ def run_ours(args):
     if rank != 0:
         return
     # ---- roofline of the dominant kernel --------------------------------------------------------
-    # tensor plans: the forward's order chain, one persistent launch per forward (stage "solve");
-    # float64 plans: the synthesis contraction (one launch per inverse)
     sm_mhz = (clk or {}).get("sm_mhz") or FP64_NOMINAL_MHZ
     peaks = _peaks()
-    syn_ms, syn_n = stages["synthesis"]          # summed ms over syn_n launches
-    syn_flops = 4.0 * B * L * L * (L + 1)        # sum_m 2 * L * (L - m) * 4B real multiply-adds
-    syn_sec = syn_ms / syn_n * 1e-3
-    # forward chain: solves sum_n 2 n^2 4B, alias products sum_m 2 m (L - m) 4B
-    chain_flops = 8.0 * B * (L * (L + 1) * (2 * L + 1) / 6.0 + (L ** 3 - L) / 6.0)
-    bf16_peak = peaks.get("bf16_tflops_sustained") or 1700.0
-    bf16_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks.get("bf16_tflops_sustained")
-                else "fallback 1.7 PFLOP/s sustained bf16")
-    if args.dtype == "f32":
-        # float32 plans: the synthesis contraction on the FP32 pipe (FFMA32): 128 lanes per SM
-        fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        achieved = syn_flops / syn_sec / 1e12
-        roof = {"bound": "alu",
-                "kernel": "k_gemm<float,64,64,4,...,MODE_SYNTH> (float32 synthesis, Eq. (11))",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                "peak_source": f"GB300 FP32 pipe: 152 SMs x 128 lanes x 2 flops at the measured median {sm_mhz:.0f} MHz",
-                "traffic": _traffic_record("synthesis_f32", L, B)}
-    elif args.dtype != "f64":
-        ch_ms, ch_n = stages["solve"]
-        ch_sec = ch_ms / ch_n * 1e-3
-        # 36 BF16 slice-pair products per float64 product (8 slices a side, s + t <= 9); the TF32
-        # chain does one TF32 product, against the TF32 peak (the measured BF16 peak times the
-        # nominal dense ratio 1.1 / 2.25 PFLOP/s)
-        slice_pairs = {"f64_tensor": 36.0, "bf16x2_refined": 3.0, "bf16_refined": 1.0, "tf32_refined": 1.0}[args.dtype]
-        achieved = slice_pairs * chain_flops / ch_sec / 1e12
-        chain_peak, chain_src = bf16_peak, bf16_src
-        if args.dtype == "tf32_refined":
-            chain_peak = bf16_peak * 1.1 / 2.25
-            chain_src = bf16_src + " x 1.1/2.25 (nominal dense TF32 / BF16)"
-        roof = {"bound": "tensor",
-                "kernel": "k_chain (forward order chain, Eqs. (14)-(16), one persistent cooperative launch; "
-                          + ("tcgen05 kind::tf32)" if args.dtype == "tf32_refined" else "tcgen05 on BF16 slices)"),
-                "achieved": achieved, "peak": chain_peak, "unit": "TFLOP/s", "frac": achieved / chain_peak,
-                "peak_source": chain_src,
-                "fp64_equivalent_tflops": chain_flops / ch_sec / 1e12,
-                "traffic": _traffic_record("chain_tc", L, B),
-                "secondary": [{
-                    "kernel": "k_synthesis (inverse, Eq. (11), TMA + tcgen05 on BF16 slices)",
-                    "bound": "tensor", "achieved": 36.0 * syn_flops / syn_sec / 1e12, "peak": bf16_peak,
-                    "unit": "TFLOP/s", "frac": 36.0 * syn_flops / syn_sec / 1e12 / bf16_peak,
-                    "fp64_equivalent_tflops": syn_flops / syn_sec / 1e12,
-                    "traffic": _traffic_record("synthesis_tc", L, B)}]}
-    else:
-        achieved = syn_flops / syn_sec / 1e12
-        peak = FP64_TFLOPS_NOMINAL
-        roof = {"bound": "alu",
-                "kernel": "k_gemm<64,64,4,0,0,1,0> (float64 synthesis, Eq. (11))",
-                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "GB300 float64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flops, 1.25 TFLOP/s at 2070 MHz; at the measured "
-                               f"median {sm_mhz:.0f} MHz the clock-scaled peak is {peak * sm_mhz / FP64_NOMINAL_MHZ:.3f}",
-                "traffic": _traffic_record("synthesis_f64", L, B)}
-    roof["stage_ms_per_step"] = {k: v[0] / stage_steps for k, v in stages.items()}
-    roof["stage_launch_spans_per_step"] = {k: v[1] / stage_steps for k, v in stages.items()}
+    roof = _roofline(args.dtype, L, B, stages, stage_steps, peaks, sm_mhz)
+
+    # ---- the other arithmetic forms on the same workload and rings (outside the timed region) ----
+    forms = None
+    if not args.no_forms and args.dtype == "f64_tensor":
+        forms = {}
+        del graph, step, step_b, sets
+        for dt, iters in (("f64", 0), ("tf32_refined", args.forms_refine_iters)):
+            forms[dt] = _time_form(dt, L, B, plan.theta, c, min(args.steps, 5), 2, iters, peaks, sm_mhz)
+
     value = _whole_job_rate(ws, B, ms)
     line = {
         "metric": METRIC, "value": value, "unit": "signals/s", "n_gpus": ws, "steps": args.steps,
@@ -459,8 +420,11 @@ def run_ours(args):
             args.dtype, "bf16 contractions + f64 residual (refined)"),
         "data": "synthetic",
         "config": dict(_config(args), parallelism=f"dp{ws}" if ws > 1 else "single GPU"),
-        "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e},
+        "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e,
+                     "definition": "max |forward(inverse(c)) - c| over the batch, both GPU transforms "
+                                   "(Exp. 1 of Sec. IV-A); GPU-vs-oracle parity is checked by the tests"},
         "roofline": roof,
+        "forms": forms,
         "cpu_baseline": cpu,
         "e2e": {"value": _whole_job_rate(ws, B, ms_e2e), "unit": "signals/s",
                 "h2d_bytes_per_step": c_host.element_size() * L * L * B,
@@ -470,6 +434,200 @@ def run_ours(args):
         "plan_seconds": plan_s,
     }
     print(json.dumps(line), flush=True)
+
+
+def _chain_flops(L, B):
+    """The method's own real flops of one forward's order chain (Eqs. (14)-(16)): the solves
+    sum_n 2 n^2 4B and the alias products sum_m 2 m (L - m) 4B."""
+    return 8.0 * B * (L * (L + 1) * (2 * L + 1) / 6.0 + (L ** 3 - L) / 6.0)
+
+
+def _synthesis_flops(L, B):
+    """Real flops of Eq. (11) for every order and ring: sum_m 2 L (L - m) 4B."""
+    return 4.0 * B * L * L * (L + 1)
+
+
+def _ring_dft_flops(L, B):
+    """float64 flops of one direction's ring DFTs, by the ring classes of csrc/dft.cu: direct
+    rings (N <= 63) 8 N^2; chirp-z rings two FFTs of the ring's convolution length M
+    (5 M log2 M each, the radix-2 count) plus the chirp and filter products (6 M + 12 N)."""
+    tot = 0.0
+    for k in range(L):
+        N = 2 * k + 1
+        if N <= 63:
+            tot += 8.0 * N * N
+            continue
+        M = _bluestein_length(N)
+        tot += 2 * 5.0 * M * math.log2(M) + 6.0 * M + 12.0 * N
+    return tot * B
+
+
+def _bluestein_length(N):
+    """Convolution length of a chirp-z ring of length N, as chosen in csrc/dft.cu."""
+    k = (N - 1) // 2
+    j = int(math.floor(math.log2(k)))
+    return 1 << (j + 3)
+
+
+def _src_hash(name):
+    import hashlib
+    path = os.path.join(ROOT, "paper_1403_4661_gb300", "csrc", name)
+    return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16] if os.path.exists(path) else None
+
+
+def _traffic(kernel, L, batch, src):
+    """DRAM bytes of one launch from profiles/traffic.txt, valid only while the kernel's source
+    file has the hash recorded with the capture (else the record is stale: None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None, "no capture recorded"
+    for line in open(path):
+        parts = dict(p.split("=", 1) for p in line.split() if "=" in p)
+        if parts.get("kernel") == kernel and parts.get("L") == str(L) and parts.get("batch") == str(batch):
+            if parts.get("src_sha") != _src_hash(src):
+                return None, f"stale: {src} changed since the capture"
+            return float(parts["dram_bytes_per_launch"]), parts.get("note", "ncu capture")
+    return None, "no capture of this kernel at this workload"
+
+
+def _roofline(dtype, L, B, stages, stage_steps, peaks, sm_mhz):
+    """Roofline entries: the dominant kernel first, then the other stages (algorithmic work per
+    launch divided by the stage's CUDA-event span, against the measured peaks)."""
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    bf16_src = ("MEASURED_PEAKS.json bf16_tflops_sustained (of measured)" if peaks.get("bf16_tflops_sustained")
+                else "fallback 1.7 PFLOP/s sustained bf16")
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    hbm_src = "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks.get("hbm_gbs") else "fallback 6.8 TB/s"
+    fp64 = FP64_TFLOPS_NOMINAL
+    fp64_src = ("GB300 float64 pipe: 152 SMs x 2 FP64 FMA per clock x 2 flops at 2070 MHz = 1.25 TFLOP/s "
+                f"(clock-scaled at the measured median {sm_mhz:.0f} MHz: {fp64 * sm_mhz / FP64_NOMINAL_MHZ:.3f})")
+
+    def span(stage):
+        ms, n = stages[stage]
+        return (ms / n * 1e-3, n) if n else (None, 0)
+
+    chain_f, syn_f = _chain_flops(L, B), _synthesis_flops(L, B)
+    entries = []
+    syn_s, _ = span("synthesis")
+    if dtype == "f32":
+        fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        a = syn_f / syn_s / 1e12
+        tr, note = _traffic("synthesis_f32", L, B, "gemm_f64.cu")
+        main = {"bound": "alu", "kernel": "k_gemm<float,64,64,4,...,MODE_SYNTH> (float32 synthesis, Eq. (11))",
+                "achieved": a, "peak": fp32, "unit": "TFLOP/s", "frac": a / fp32,
+                "peak_source": f"GB300 FP32 pipe: 152 SMs x 128 lanes x 2 flops at {sm_mhz:.0f} MHz",
+                "flops_per_launch": syn_f, "traffic": tr, "traffic_note": note}
+    elif dtype == "f64":
+        a = syn_f / syn_s / 1e12
+        tr, note = _traffic("synthesis_f64", L, B, "gemm_f64.cu")
+        main = {"bound": "alu", "kernel": "k_gemm<double,64,64,4,...,MODE_SYNTH> (float64 synthesis, Eq. (11))",
+                "achieved": a, "peak": fp64, "unit": "TFLOP/s", "frac": a / fp64, "peak_source": fp64_src,
+                "flops_per_launch": syn_f, "traffic": tr, "traffic_note": note}
+    else:
+        ch_s, ch_n = span("solve")
+        tf32 = dtype == "tf32_refined"
+        peak = bf16 * 1.1 / 2.25 if tf32 else bf16
+        a = chain_f / ch_s / 1e12
+        pairs = {"f64_tensor": 36.0, "bf16x2_refined": 3.0, "bf16_refined": 1.0, "tf32_refined": 1.0}[dtype]
+        tr, note = _traffic("chain_tf32" if tf32 else "chain_tc", L, B, "chain.cu")
+        main = {"bound": "tensor",
+                "kernel": "k_chain (forward order chain, Eqs. (14)-(16), one persistent cooperative launch; "
+                          + ("tcgen05 kind::tf32)" if tf32 else "tcgen05 on BF16 slices)"),
+                "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak,
+                "peak_source": bf16_src + (" x 1.1/2.25 (nominal dense TF32 / BF16)" if tf32 else ""),
+                "flops_per_launch": chain_f,
+                "flops_definition": "the method's own real flops: solves sum_n 2 n^2 4B + alias products "
+                                    "sum_m 2 m (L-m) 4B = 8B[L(L+1)(2L+1)/6 + (L^3-L)/6]",
+                "launches_per_step": ch_n / stage_steps,
+                "mma_issue": {"products_per_method_product": pairs, "achieved": pairs * a, "unit": "TFLOP/s",
+                              "frac": pairs * a / peak,
+                              "note": "rate of the tensor-core products actually issued (slice pairs)"},
+                "vs_fp64_pipe": a / fp64,
+                "traffic": tr, "traffic_note": note}
+        if syn_s:
+            sa = syn_f / syn_s / 1e12
+            entries.append({"stage": "synthesis", "kernel": "k_synthesis (Eq. (11), TMA + tcgen05 on BF16 slices)",
+                            "bound": "tensor", "achieved": sa, "peak": bf16, "unit": "TFLOP/s", "frac": sa / bf16,
+                            "flops_per_launch": syn_f, "mma_issue_tflops": 36.0 * sa,
+                            "vs_fp64_pipe": sa / fp64})
+    eb = 8 if dtype == "f32" else 16
+    dft_f = _ring_dft_flops(L, B)
+    for stage, kern, byts in (("ring_dft", "k_ring_dft (forward ring DFTs into order-major bins)",
+                               2.0 * eb * L * L * B),
+                              ("ring_idft", "k_ring_idft (fold of the orders into ring bins + inverse ring DFTs)",
+                               eb * (2 * L * L - L) * B + eb * L * L * B)):
+        t, n = span(stage)
+        if not t:
+            continue
+        per = n / stage_steps
+        gbs = byts / (t * per) / 1e9
+        fl = dft_f / (t * per) / 1e12
+        entries.append({"stage": stage, "kernel": kern, "bound": "hbm", "achieved": gbs, "peak": hbm,
+                        "unit": "GB/s", "frac": gbs / hbm, "peak_source": hbm_src, "bytes_per_step": byts,
+                        "fp64_alu": {"achieved": fl, "peak": fp64, "unit": "TFLOP/s", "frac": fl / fp64,
+                                     "flops_per_step": dft_f,
+                                     "note": "the DFTs are float64-pipe bound: chirp-z FFT flops per step"}
+                        if dtype != "f32" else None})
+    main["secondary"] = entries
+    main["stage_ms_per_step"] = {k: v[0] / stage_steps for k, v in stages.items()}
+    main["stage_launch_spans_per_step"] = {k: v[1] / stage_steps for k, v in stages.items()}
+    return main
+
+
+def _time_form(dtype, L, B, theta, c, steps, warmup, refine_iters, peaks, sm_mhz):
+    """Step rate of another arithmetic on the same workload and rings: one CUDA graph per step
+    (inverse then forward), CUDA events on the launching stream, stage spans of the last replay."""
+    import torch
+    from paper_1403_4661_gb300.sht import Plan
+
+    t0 = time.time()
+    plan = Plan(L, theta=theta, dtype=dtype)
+    plan_s = time.time() - t0
+    if dtype.endswith("refined"):
+        plan.set_refinement(refine_iters, 0.0)   # fixed iteration count: capturable
+    plan.reserve(B)
+    s = torch.empty_like(c)
+    c2 = torch.empty_like(c)
+
+    def run():
+        plan.inverse(c, out=s)
+        plan.forward(s, out=c2)
+
+    for _ in range(warmup):
+        run()
+    torch.cuda.synchronize()
+    err = (c2 - c).abs().max().item()
+    plan.set_timing(True)
+    plan.stage_times()
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            run()
+    torch.cuda.current_stream().wait_stream(side)
+    plan.set_timing(False)
+    for _ in range(2):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    stages = plan.stage_times()
+    roof = _roofline(dtype, L, B, stages, 1, peaks, sm_mhz)
+    out = {"value": B / (ms * 1e-3), "unit": "signals/s", "ms_per_step": ms, "steps": steps,
+           "E1_max_round_trip": err, "plan_seconds": plan_s, "roofline": roof}
+    if dtype.endswith("refined"):
+        out["refine_iterations"] = refine_iters
+    del g
+    plan.close()
+    torch.cuda.synchronize()
+    return out
 
 
 def main():
@@ -486,6 +644,11 @@ def main():
     ap.add_argument("--refine-iters", type=int, default=0,
                     help="refined forms: fixed iteration count (0: iterate to 1e-12)")
     ap.add_argument("--no-graph", action="store_true", help="launch eagerly instead of one CUDA graph per step")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip timing the f64 and tf32_refined forms of the same workload")
+    ap.add_argument("--forms-refine-iters", type=int, default=5,
+                    help="fixed iteration count of the tf32_refined form (5 reaches the float64 "
+                         "path's round-trip error at L=1024)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

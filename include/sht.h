@@ -223,17 +223,22 @@ sht_status sht_forward_adjoint(sht_plan_t plan, const void *d_coeffs, void *d_sa
  *   (a library embedded in a host application that hands it a fixed memory budget, or code that
  *   runs where cudaMalloc is not allowed, e.g. while other work is being captured into a CUDA
  *   graph).  The paper has no counterpart: this is a deployment variant of sht_forward.
- *   Same arguments, layouts and result as sht_forward (a plan created beforehand; device buffers
- *   owned by the caller).  Its scratch - the bins, the solved orders and the split-K partial
- *   sums - lives in one fixed 64 MiB __device__ array of the library instead of the plan's
- *   workspaces, so the call allocates nothing.  Sizes whose scratch exceeds 64 MiB
- *   (2 * 32 * L(L+1)/2 * batch + 512 * L * batch bytes, about L = 1024 for one signal) return
- *   SHT_ERR_UNSUPPORTED with the required size in sht_last_error_message.
+ *   Same arguments, layouts and argument checks as sht_forward (a plan created beforehand; device
+ *   buffers owned by the caller).  Whatever the plan's arithmetic, it runs the float64 SIMT order
+ *   chain on the plan's float64 tables: float64-accurate (within 1e-11 of sht_forward on the
+ *   workloads tested), but not bit-identical to the tensor-core chain of SHT_F64_TENSOR or to a
+ *   refined forward; SHT_F32 plans are refused (SHT_ERR_UNSUPPORTED).  Its scratch - the bins,
+ *   the solved orders and the split-K partial sums - lives in one fixed 64 MiB (67108864-byte)
+ *   __device__ array of the library instead of the plan's workspaces, so the call allocates
+ *   nothing.  It needs 2 * r256(32 * L(L+1)/2 * batch) + r256(512 * L * batch) bytes, r256
+ *   rounding up to a multiple of 256: for example L = 1024 with batch 1 fits and batch 2 does not.
+ *   Larger sizes return SHT_ERR_UNSUPPORTED with the required size in sht_last_error_message.
  *   The array exists on every GPU that loads the library until the process exits.  All calls on
  *   a device share it and leave their contents in it (nothing needs to start at zero: every
  *   element read is written earlier in the same call); calls whose GPU work overlaps in time race.
- *   The first call on each device looks up the array's device address (cudaGetSymbolAddress),
- *   so make that first call before any stream capture.
+ *   The first call in each CUDA context looks up the array's device address
+ *   (cudaGetSymbolAddress) and keeps it with the context's unique id, so make that first call
+ *   before any stream capture; after cudaDeviceReset the next call looks it up again.
  */
 sht_status sht_forward_noalloc(sht_plan_t plan, const void *d_samples, void *d_coeffs,
                                int64_t batch, void *stream);

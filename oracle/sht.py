@@ -45,11 +45,12 @@ def _coeff_index(l, m):
     return l * l + l + m
 
 
-def inverse(coeffs, L, theta, m_lo=0):
+def inverse(coeffs, L, theta, m_lo=0, orders=None):
     """Samples from coefficients by Procedure 2.  coeffs: (B, L^2) or (L^2,) complex.
 
-    m_lo > 0 runs only the iterations m >= m_lo of the procedure's loop (a bounded sample of its
-    work, used to time the oracle at large L); the result is then a partial sum.
+    m_lo > 0 runs only the iterations m >= m_lo of the procedure's loop; ``orders`` (an iterable of
+    m) runs only those iterations.  Either gives a bounded sample of the work, used to time the
+    oracle at large L; the result is then a partial sum.
     """
     c = np.atleast_2d(np.asarray(coeffs, dtype=np.complex128))
     theta = np.asarray(theta, dtype=np.float64)
@@ -57,7 +58,7 @@ def inverse(coeffs, L, theta, m_lo=0):
     f = np.zeros((Bn, L * L), dtype=np.complex128)
     bases = sectoral_bases(L, theta)
     layout = sample_ring_index(L)
-    for m in range(m_lo, L):
+    for m in (range(m_lo, L) if orders is None else sorted(set(orders))):
         # step 1: P~_l^m(theta_k), P~_l^{-m} = (-1)^m P~_l^m, all k, l = m..L-1
         P = ptilde_order(m, L, theta, bases)            # (L rings, L - m)
         ell = np.arange(m, L)
@@ -75,11 +76,13 @@ def inverse(coeffs, L, theta, m_lo=0):
     return f if np.ndim(coeffs) == 2 else f[0]
 
 
-def forward(samples, L, theta, m_lo=0):
+def forward(samples, L, theta, m_lo=0, orders=None):
     """Coefficients from samples by Procedure 1.  samples: (B, L^2) or (L^2,) complex.
 
-    m_lo > 0 stops the procedure's loop after the iteration m = m_lo (a bounded sample of its
-    work, used to time the oracle at large L); coefficients of orders |m| < m_lo are then 0.
+    m_lo > 0 stops the procedure's loop after the iteration m = m_lo; ``orders`` (an iterable of
+    m) runs only those iterations, in the procedure's order.  Either gives a bounded sample of the
+    work, used to time the oracle at large L; coefficients of the skipped orders are then 0 and
+    the others are not those of the full procedure.
     """
     s = np.atleast_2d(np.asarray(samples, dtype=np.complex128))
     theta = np.asarray(theta, dtype=np.float64)
@@ -89,7 +92,7 @@ def forward(samples, L, theta, m_lo=0):
     bases = sectoral_bases(L, theta)
     layout = sample_ring_index(L)
     ring_start = np.arange(L, dtype=np.int64) ** 2
-    for m in range(L - 1, m_lo - 1, -1):
+    for m in (range(L - 1, m_lo - 1, -1) if orders is None else sorted(set(orders), reverse=True)):
         P = ptilde_order(m, L, theta, bases)            # P~_l^m(theta_k), all k, l = m..L-1
         ell = np.arange(m, L)
         # step 3: g_{+-m}[k] = (2 pi / N_k) sum_n f(theta_k, phi_n) e^{-+ i m phi_n}, k = m..L-1

@@ -25,6 +25,34 @@ sht_status cuda_check(cudaError_t e, const char *what) {
     return SHT_ERR_CUDA;
 }
 
+// Elements of one complex value of the plan's signals: complex64 for SHT_F32, else complex128.
+static int64_t plan_elem_bytes(sht_plan_t p) { return p->dtype == SHT_F32 ? 8 : 16; }
+
+sht_status check_plan(sht_plan_t p) {
+    if (!p) return set_error(SHT_ERR_INVALID_ARG, "plan is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
+    if (dev != p->device) return set_error(SHT_ERR_INVALID_ARG, "current device is not the plan's device");
+    return SHT_OK;
+}
+
+sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch) {
+    sht_status st = check_plan(p);
+    if (st != SHT_OK) return st;
+    if (batch < 0 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [0, 65535]");
+    if (batch == 0) return SHT_OK;
+    if (!in || !out) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");
+    const uintptr_t eb = (uintptr_t)plan_elem_bytes(p);   // alignment: one complex element
+    if (((uintptr_t)in & (eb - 1)) || ((uintptr_t)out & (eb - 1)))
+        return set_error(SHT_ERR_INVALID_ARG, eb == 16 ? "buffers must be 16-byte aligned"
+                                                       : "buffers must be 8-byte aligned");
+    const uintptr_t bytes = eb * (uintptr_t)p->L * (uintptr_t)p->L * (uintptr_t)batch;
+    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
+    if (a < b + bytes && b < a + bytes) return set_error(SHT_ERR_INVALID_ARG, "input and output overlap");
+    return SHT_OK;
+}
+
 }  // namespace sht
 
 using namespace sht;
@@ -32,7 +60,6 @@ using namespace sht;
 namespace {
 
 constexpr int kMaxL = 2048;           // longest ring 4095 -> Bluestein length 8192 in shared memory
-constexpr int64_t kMaxBatch = 65535;  // batch is a grid dimension of the ring kernels
 
 void free_ws(Workspace &w) {
     cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
@@ -265,31 +292,6 @@ struct Span {
         }
     }
 };
-
-sht_status check_plan(sht_plan_t p) {
-    if (!p) return set_error(SHT_ERR_INVALID_ARG, "plan is NULL");
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
-    if (dev != p->device) return set_error(SHT_ERR_INVALID_ARG, "current device is not the plan's device");
-    return SHT_OK;
-}
-
-sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch) {
-    sht_status st = check_plan(p);
-    if (st != SHT_OK) return st;
-    if (batch < 0 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [0, 65535]");
-    if (batch == 0) return SHT_OK;
-    if (!in || !out) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");
-    const uintptr_t eb = (uintptr_t)elem_bytes(p);   // alignment: one complex element
-    if (((uintptr_t)in & (eb - 1)) || ((uintptr_t)out & (eb - 1)))
-        return set_error(SHT_ERR_INVALID_ARG, eb == 16 ? "buffers must be 16-byte aligned"
-                                                       : "buffers must be 8-byte aligned");
-    const uintptr_t bytes = eb * (uintptr_t)p->L * (uintptr_t)p->L * (uintptr_t)batch;
-    const uintptr_t a = (uintptr_t)in, b = (uintptr_t)out;
-    if (a < b + bytes && b < a + bytes) return set_error(SHT_ERR_INVALID_ARG, "input and output overlap");
-    return SHT_OK;
-}
 
 // The execution choices recorded for this batch size (sht_plan_set_paths / sht_plan_autotune).
 const sht_tuning *tuning_for(sht_plan_t p, int64_t batch) {

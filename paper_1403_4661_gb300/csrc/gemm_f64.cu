@@ -18,8 +18,20 @@ namespace sht {
 namespace {
 
 constexpr int BK = 16;
-constexpr int kSMs = 152;
 constexpr int kMaxSplit = 16;
+
+// Streaming multiprocessors of the current device (looked up once per device; 152 on GB300).
+int sm_count() {
+    static int cached[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!cached[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached[dev] = n;
+    }
+    return cached[dev];
+}
 
 enum Mode : int { MODE_SINGLE = 0, MODE_SYNTH = 1, MODE_ANALYSIS = 2 };
 
@@ -207,6 +219,7 @@ template <typename T, bool TA, int EPI>
 cudaError_t launch_single(Params<T> p, cudaStream_t s, T *part, int64_t part_cap, int64_t *count,
                           int split_cap) {
     const int cap = split_cap > 0 ? std::min(split_cap, kMaxSplit) : kMaxSplit;
+    const int kSMs = sm_count();
     Cfg c{64, 64};
     if (p.N <= 32) {
         c = Cfg{16, 16};

@@ -158,6 +158,13 @@ namespace sht {
 sht_status set_error(sht_status st, const std::string &msg);
 sht_status cuda_check(cudaError_t e, const char *what);
 
+// Largest batch of one call: the batch is a grid dimension of the ring kernels.
+constexpr int64_t kMaxBatch = 65535;
+// Argument checks shared by the entry points (api.cu): plan non-NULL and on the current device;
+// batch in [0, kMaxBatch]; for batch > 0, non-NULL buffers aligned to one element and disjoint.
+sht_status check_plan(sht_plan_t p);
+sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch);
+
 // legendre.cu: P~ table for arbitrary co-latitudes (rows), all orders.
 cudaError_t build_ptilde_table(int L, const double *d_theta_rows, int nrows, double *d_table,
                                cudaStream_t s);

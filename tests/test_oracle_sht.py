@@ -118,6 +118,24 @@ def test_evaluate_samples_matches_inverse():
     np.testing.assert_allclose(sht.evaluate_samples(c, L, th, idx), sht.inverse(c, L, th)[:, idx], atol=1e-13)
 
 
+@pytest.mark.parametrize("L", [1, 5, 17, 40])
+def test_evaluate_at_arbitrary_points_matches_scipy(L):
+    """Eq. (6) at random (theta, phi), not on the sampling grid: the oracle's evaluate against the
+    plain sum of scipy's Y_l^m (Condon-Shortley phase, orthonormal, Eq. (29))."""
+    from scipy.special import sph_harm_y
+
+    rng = np.random.default_rng(L)
+    th = np.concatenate([[0.0, math.pi, 1e-3, math.pi / 2], rng.uniform(0, math.pi, 12)])
+    ph = np.concatenate([[0.3, 2.0, 6.0, 0.0], rng.uniform(0, 2 * math.pi, 12)])
+    c = synth.uniform_coeffs(L, 2, 40 + L)
+    ref = np.zeros((2, th.size), dtype=np.complex128)
+    for l in range(L):
+        for m in range(-l, l + 1):
+            ref += c[:, l * l + l + m][:, None] * sph_harm_y(l, m, th, ph)[None, :]
+    got = sht.evaluate(c, L, th, ph)
+    np.testing.assert_allclose(got, ref, atol=1e-12 * max(1, L))
+
+
 # --- planted mistakes: each plausible error in the oracle must fail a pin above -------------
 
 def test_planted_mistakes_are_caught(monkeypatch):
