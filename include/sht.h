@@ -130,6 +130,32 @@ sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host
                                 sht_plan_t *out);
 
 /*
+ * sht_plan_spin, sht_plan_spin_with_thetas - plans for spin-s functions (Sec. III-H: the transforms
+ *   carry over with f -> sf, f_l^m -> sf_l^m, Y_l^m -> sY_l^m; Appendix A defines
+ *   sY_l^m(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) e^{i m phi} d^l_{m,-s}(theta), the Wigner small-d
+ *   function d computed by its three-term recursion in l (Appendix A)).  Same sampling and ring
+ *   orderings as sht_plan / sht_plan_with_thetas (flags and theta_host as there).
+ *   spin: -8..8, non-zero, |spin| < L; L in 1..1024; dtype SHT_F64 only (SHT_ERR_UNSUPPORTED
+ *   otherwise).  Coefficients use the scalar layout (index l^2 + l + m); the entries with l < |s|
+ *   are ignored on input and written as 0.  The plan holds the tables of both signs of m (there is
+ *   no P_{-m} = (-1)^m P_m relation for s != 0): twice the float64 tables of a scalar plan.  For
+ *   |m| >= |s| the order-m systems are square and inverted; for |m| < |s| they have more rings
+ *   than degrees and the forward solves them in the least-squares sense (exact for band-limited
+ *   spin signals).
+ *   Entry points on spin plans: sht_forward, sht_inverse, sht_inverse_adjoint.  The others
+ *   (sht_forward_adjoint, sht_forward_noalloc, the uneven calls, sht_plan_set_paths,
+ *   sht_plan_autotune, sht_plan_save) return SHT_ERR_UNSUPPORTED.
+ *   Accuracy: the inverse and its adjoint are plain sums (float64 rounding).  The forward follows
+ *   Procedure 1, whose order-by-order elimination amplifies rounding errors far more for s != 0
+ *   than for s = 0 on these rings (measured round-trip errors: about 3e-10 at L = 16, s = 1, and
+ *   order 1 at L = 16, s = 2, while the whole L^2-dimensional system stays well conditioned there);
+ *   it is meant for small L.
+ */
+sht_status sht_plan_spin(int L, int spin, sht_dtype dtype, uint32_t flags, sht_plan_t *out);
+sht_status sht_plan_spin_with_thetas(int L, int spin, sht_dtype dtype, const double *theta_host,
+                                     uint32_t flags, sht_plan_t *out);
+
+/*
  * sht_plan_save, sht_plan_load - keep a plan's ring co-latitudes on disk, so that a later process
  *   skips the greedy ordering (Sec. III-E; O(L^4), 23 s at L = 1024 on GB300) and rebuilds only the
  *   tables.  The paper stores the co-latitudes once per L for the same reason (Sec. III-E).
@@ -326,6 +352,7 @@ typedef struct {
     int64_t kernel_launches;   /* kernels this plan's transform calls have launched so far */
     int refine_iterations;     /* refined forward: iterations of the most recent call */
     double refine_last_update; /* refined forward: largest |Re|, |Im| of its last update (tol > 0) */
+    int spin;                  /* spin weight s of the plan (0: scalar functions) */
 } sht_info;
 
 /* Stages of the transforms, for sht_plan_stage_times. */

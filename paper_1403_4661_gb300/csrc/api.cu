@@ -60,6 +60,8 @@ using namespace sht;
 namespace {
 
 constexpr int kMaxL = 2048;           // longest ring 4095 -> Bluestein length 8192 in shared memory
+constexpr int kMaxSpinL = 1024;       // spin plans: host least-squares pseudo-inverses for |m| < |s|
+constexpr int kMaxSpin = 8;
 
 void free_ws(Workspace &w) {
     cudaFree(w.a); cudaFree(w.b); cudaFree(w.g); cudaFree(w.part);
@@ -73,7 +75,7 @@ void destroy(sht_plan_t p) {
     int dev = -1;
     cudaGetDevice(&dev);
     if (dev != p->device) cudaSetDevice(p->device);
-    cudaFree(p->d_theta); cudaFree(p->pt); cudaFree(p->pinv);
+    cudaFree(p->d_theta); cudaFree(p->pt); cudaFree(p->pinv); cudaFree(p->pt2); cudaFree(p->pinv2);
     cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
     cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
     cudaFree(p->d_tmaps);
@@ -185,11 +187,12 @@ sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
 }
 
 sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, double order_s,
-                      sht_plan_t *out) {
+                      sht_plan_t *out, int spin = 0) {
     auto t0 = std::chrono::steady_clock::now();
     sht_plan_t p = new sht_plan_s;
     p->L = L;
     p->dtype = (int)dtype;
+    p->spin = spin;
     p->theta = theta;
     p->order_seconds = order_s;
     cudaGetDevice(&p->device);
@@ -205,13 +208,28 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
         (e = cudaMalloc(&p->pinv, pi_bytes)) != cudaSuccess) {
         st = cuda_check(e, "plan table allocation");
     }
-    if (st == SHT_OK) {
+    if (st == SHT_OK && spin != 0) {
+        // spin-s tables of both signs of m and their (pseudo-)inverses (Sec. III-H)
+        bool singular = false;
+        if ((e = cudaMalloc(&p->pt2, pt_bytes)) != cudaSuccess || (e = cudaMalloc(&p->pinv2, pi_bytes)) != cudaSuccess) {
+            st = cuda_check(e, "spin table allocation");
+        } else {
+            cudaMemcpyAsync(p->d_theta, theta.data(), sizeof(double) * L, cudaMemcpyHostToDevice, s);
+            e = build_spin_tables(L, spin, p->d_theta, p->pt, p->pt2, p->pinv, p->pinv2, singular, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (singular)
+                st = set_error(SHT_ERR_INVALID_ARG, "a per-order spin matrix is singular for these co-latitudes");
+            else if (e != cudaSuccess)
+                st = cuda_check(e, "spin tables");
+        }
+    }
+    if (st == SHT_OK && spin == 0) {
         cudaMemcpyAsync(p->d_theta, theta.data(), sizeof(double) * L, cudaMemcpyHostToDevice, s);
         e = build_ptilde_table(L, p->d_theta, L, p->pt, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_check(e, "Legendre table");
     }
-    if (st == SHT_OK) {
+    if (st == SHT_OK && spin == 0) {
         e = build_inverses(L, p->pt, p->pinv, s);
         if (e == cudaErrorInvalidValue)
             st = set_error(SHT_ERR_INVALID_ARG, "a per-order matrix P_m is singular for these co-latitudes");
@@ -250,7 +268,7 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
     if (st == SHT_OK && tensor_plan(p)) st = build_tensor_tables(p, s, tc_bytes);
     cudaStreamDestroy(s);
     if (st != SHT_OK) { destroy(p); *out = nullptr; return st; }
-    p->table_bytes = pt_bytes + pi_bytes + dft_bytes + tc_bytes + f32_bytes + sizeof(double) * L;
+    p->table_bytes = (spin ? 2 : 1) * (pt_bytes + pi_bytes) + dft_bytes + tc_bytes + f32_bytes + sizeof(double) * L;
     p->plan_seconds = order_s + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
     return SHT_OK;
@@ -560,6 +578,7 @@ sht_status uneven(bool forward, const sht_plan_t *plans, int nplans, int64_t nsi
         if (st != SHT_OK) return st;
         if (plans[g]->dtype == SHT_F32)
             return set_error(SHT_ERR_UNSUPPORTED, "uneven batches take complex128 plans (not SHT_F32)");
+        if (plans[g]->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "uneven batches take scalar (spin-0) plans");
     }
     // signals as intervals [offset, offset + L^2) of complex elements: in range, disjoint
     std::vector<std::pair<int64_t, int64_t>> iv((size_t)nsig);
@@ -714,11 +733,11 @@ sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host
     return build_plan(L, dtype, th, 0.0, out);
 }
 
-sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
-    if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
-    if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+}  // extern "C"
+
+// The ordered ring co-latitudes of sht_plan's flags (Sec. III-E, III-F); order_s receives the time
+// the ordering took.
+static sht_status ordered_rings(int L, uint32_t flags, std::vector<double> &th, double &order_s) {
     const uint32_t measure = flags & SHT_MEASURE_MASK;
     if (measure != SHT_MEASURE_UNIFORM && measure != SHT_MEASURE_SIN && measure != SHT_MEASURE_TAN13)
         return set_error(SHT_ERR_INVALID_ARG, "unknown ring measure in flags");
@@ -736,10 +755,58 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
                                      uniform ? 0.0 : 1e-9, order);
         if (st != SHT_OK) return st;
     }
-    double order_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    std::vector<double> th(L);
+    order_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    th.assign((size_t)L, 0.0);
     for (int k = 0; k < L; ++k) th[k] = Theta[order[k]];
+    return SHT_OK;
+}
+
+static sht_status check_spin_args(int L, int spin, sht_dtype dtype) {
+    if (L < 1 || L > kMaxSpinL) return set_error(SHT_ERR_UNSUPPORTED, "spin plans take L in [1, 1024]");
+    if (spin == 0 || spin < -kMaxSpin || spin > kMaxSpin)
+        return set_error(SHT_ERR_UNSUPPORTED, "spin must be in [-8, 8] and non-zero (use sht_plan for s = 0)");
+    if (std::abs(spin) >= L) return set_error(SHT_ERR_INVALID_ARG, "|spin| must be below L");
+    if (dtype != SHT_F64) return set_error(SHT_ERR_UNSUPPORTED, "spin plans run the SHT_F64 arithmetic only");
+    return SHT_OK;
+}
+
+extern "C" {
+
+sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
+    if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
+    if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    std::vector<double> th;
+    double order_s = 0.0;
+    sht_status st = ordered_rings(L, flags, th, order_s);
+    if (st != SHT_OK) return st;
     return build_plan(L, dtype, th, order_s, out);
+}
+
+sht_status sht_plan_spin(int L, int spin, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
+    if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sht_status st = check_spin_args(L, spin, dtype);
+    if (st != SHT_OK) return st;
+    std::vector<double> th;
+    double order_s = 0.0;
+    if ((st = ordered_rings(L, flags, th, order_s)) != SHT_OK) return st;
+    return build_plan(L, dtype, th, order_s, out, spin);
+}
+
+sht_status sht_plan_spin_with_thetas(int L, int spin, sht_dtype dtype, const double *theta_host, uint32_t flags,
+                                     sht_plan_t *out) {
+    (void)flags;
+    if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    sht_status st = check_spin_args(L, spin, dtype);
+    if (st != SHT_OK) return st;
+    if (!theta_host) return set_error(SHT_ERR_INVALID_ARG, "theta_host is NULL");
+    std::vector<double> th(theta_host, theta_host + L);
+    for (double t : th)
+        if (!(t >= -1e-12 && t <= M_PI + 1e-12)) return set_error(SHT_ERR_INVALID_ARG, "theta outside [0, pi]");
+    return build_plan(L, dtype, th, 0.0, out, spin);
 }
 
 // 64-bit FNV-1a over a byte range (the file hash of sht_plan_save / sht_plan_load).
@@ -751,6 +818,7 @@ static const char kThetaTag[8] = {'S', 'H', 'T', 'T', 'H', 'E', 'T', 'A'};
 
 sht_status sht_plan_save(sht_plan_t p, const char *path) {
     if (!p || !path) return set_error(SHT_ERR_INVALID_ARG, "NULL argument");
+    if (p->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "sht_plan_save: scalar (spin-0) plans only");
     std::vector<unsigned char> buf(16 + 8 * (size_t)p->L);
     std::memcpy(buf.data(), kThetaTag, 8);
     const int32_t hdr[2] = {p->L, 0};
@@ -828,6 +896,7 @@ sht_status sht_get_info(sht_plan_t p, sht_info *out) {
     out->kernel_launches = p->launches;
     out->refine_iterations = p->refine_iters;
     out->refine_last_update = p->refine_last;
+    out->spin = p->spin;
     return SHT_OK;
 }
 
@@ -851,6 +920,7 @@ sht_status sht_plan_set_refinement(sht_plan_t p, int max_iters, double tol) {
 sht_status sht_plan_set_paths(sht_plan_t p, int64_t batch, int forward_path, int inverse_path, int split_cap) {
     sht_status st = check_plan(p);
     if (st != SHT_OK) return st;
+    if (p->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "spin plans have one execution path");
     if (batch < 1 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [1, 65535]");
     if (split_cap < 0 || split_cap > 16) return set_error(SHT_ERR_INVALID_ARG, "split_cap outside 0..16");
     const bool tensor = tensor_plan(p), refined = p->refine_nsl > 0;
@@ -873,6 +943,7 @@ sht_status sht_plan_set_paths(sht_plan_t p, int64_t batch, int forward_path, int
 sht_status sht_plan_autotune(sht_plan_t p, int64_t batch, sht_tuning *out) {
     sht_status st = check_plan(p);
     if (st != SHT_OK) return st;
+    if (p->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "spin plans have one execution path");
     if (batch < 1 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [1, 65535]");
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     const bool tensor = tensor_plan(p), refined = p->refine_nsl > 0;
@@ -993,6 +1064,8 @@ sht_status sht_forward(sht_plan_t p, const void *d_samples, void *d_coeffs, int6
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->spin != 0)
+        return cuda_check(spin_forward(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s), "sht_forward (spin)");
     if (p->dtype == SHT_F32)
         return cuda_check(forward_f32(p, p->ws, (const float2 *)d_samples, (float2 *)d_coeffs, batch, s), "sht_forward");
     if (p->refine_nsl > 0) return refined_forward(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s);
@@ -1006,6 +1079,9 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     sht_status st = check_io(p, d_coeffs, d_samples, batch);
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
+    if (p->spin != 0)
+        return cuda_check(spin_inverse(p, (const double2 *)d_coeffs, (double2 *)d_samples, batch, (cudaStream_t)stream),
+                          "sht_inverse (spin)");
     if (p->dtype == SHT_F32)
         return cuda_check(simt_inverse<float>(p, p->ws, (const float2 *)d_coeffs, (float2 *)d_samples, batch,
                                               (cudaStream_t)stream),
@@ -1031,6 +1107,9 @@ sht_status sht_inverse_adjoint(sht_plan_t p, const void *d_samples, void *d_coef
     if (st != SHT_OK || batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->spin != 0)
+        return cuda_check(spin_inverse_adjoint(p, (const double2 *)d_samples, (double2 *)d_coeffs, batch, s),
+                          "sht_inverse_adjoint (spin)");
     const cudaError_t e =
         p->dtype == SHT_F32
             ? simt_inverse_adjoint<float>(p, (const float2 *)d_samples, (float2 *)d_coeffs, batch, s)
@@ -1041,7 +1120,9 @@ sht_status sht_inverse_adjoint(sht_plan_t p, const void *d_samples, void *d_coef
 sht_status sht_forward_adjoint(sht_plan_t p, const void *d_coeffs, void *d_samples, int64_t batch,
                                void *stream) {
     sht_status st = check_io(p, d_coeffs, d_samples, batch);
-    if (st != SHT_OK || batch == 0) return st;
+    if (st != SHT_OK) return st;
+    if (p->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "sht_forward_adjoint: not offered for spin plans");
+    if (batch == 0) return st;
     if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
     const cudaError_t e =

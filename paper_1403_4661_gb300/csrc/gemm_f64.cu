@@ -49,6 +49,7 @@ struct Params {
     const T *pt; const T *X; T *Y;  // grouped modes
     T *part;            // split-K partial sums [split][M][N]
     int splits, kchunk;
+    int slots;          // epilogue column pairs (bit 0: +m, bit 1: -m)
 };
 
 // sum_{j=1..x} ceil(j / bm)
@@ -60,7 +61,7 @@ __host__ __device__ __forceinline__ int64_t ceil_sum(int64_t x, int64_t bm) {
 template <int EPI, typename T>
 __device__ __forceinline__ void epilogue(const Params<T> &p, T *C, int64_t ldc, int m, int N,
                                          int r, int c0, const T v[4]) {
-    EpiArgsT<T> e{C, ldc, p.C0, m, p.L, N, p.coeffs, p.W};
+    EpiArgsT<T> e{C, ldc, p.C0, m, p.L, N, p.coeffs, p.W, p.slots};
     epilogue_row4<EPI>(e, r, c0, v);
 }
 
@@ -255,6 +256,7 @@ cudaError_t gemm_t(bool transA, int M, int K, int N, const T *A, int64_t lda, co
     Params<T> p{};
     p.A = A; p.lda = lda; p.B = B; p.ldb = ldb; p.C = C; p.ldc = ldc; p.C0 = C0;
     p.M = M; p.K = K; p.N = N; p.m = ga.m; p.L = ga.L; p.coeffs = ga.coeffs; p.W = ga.W;
+    p.slots = ga.slots;
 #define SHT_GEMM_CASE(E)                                                                        \
     if (epi == E) return transA ? launch_single<T, true, E>(p, s, ga.part, ga.part_cap, ga.launches, ga.split_cap) \
                                 : launch_single<T, false, E>(p, s, ga.part, ga.part_cap, ga.launches, ga.split_cap);
@@ -267,18 +269,18 @@ cudaError_t gemm_t(bool transA, int M, int K, int N, const T *A, int64_t lda, co
 }
 
 template <typename T>
-cudaError_t synthesis_t(int L, int64_t batch, const T *pt, const T *X, T *Gt, cudaStream_t s) {
+cudaError_t synthesis_t(int L, int64_t batch, const T *pt, const T *X, T *Gt, cudaStream_t s, int slots = 3) {
     Params<T> p{};
-    p.L = L; p.N = (int)(4 * batch); p.pt = pt; p.X = X; p.Y = Gt;
+    p.L = L; p.N = (int)(4 * batch); p.pt = pt; p.X = X; p.Y = Gt; p.slots = slots;
     Cfg c = p.N <= 32 ? Cfg{16, 16} : Cfg{64, 64};
     const int64_t tiles = (int64_t)L * cdiv(L, c.bm) * cdiv(p.N, c.bn);
     return launch_cfg<T, false, EPI_STORE, MODE_SYNTH, false>(p, c, dim3((unsigned)tiles), s);
 }
 
 template <typename T>
-cudaError_t analysis_t(int L, int64_t batch, const T *pt, const T *U, T *X, cudaStream_t s) {
+cudaError_t analysis_t(int L, int64_t batch, const T *pt, const T *U, T *X, cudaStream_t s, int slots = 3) {
     Params<T> p{};
-    p.L = L; p.N = (int)(4 * batch); p.pt = pt; p.X = U; p.Y = X;
+    p.L = L; p.N = (int)(4 * batch); p.pt = pt; p.X = U; p.Y = X; p.slots = slots;
     Cfg c = p.N <= 32 ? Cfg{16, 16} : Cfg{64, 64};
     const int64_t tiles = cdiv(p.N, c.bn) * ceil_sum(L, c.bm);
     return launch_cfg<T, true, EPI_STORE, MODE_ANALYSIS, false>(p, c, dim3((unsigned)tiles), s);
@@ -311,6 +313,14 @@ cudaError_t analysis_all_orders(int L, int64_t batch, const double *pt, const do
 cudaError_t analysis_all_orders(int L, int64_t batch, const float *pt, const float *U,
                                 float *X, cudaStream_t s) {
     return analysis_t<float>(L, batch, pt, U, X, s);
+}
+cudaError_t synthesis_all_orders_slots(int L, int64_t batch, const double *pt, const double *X,
+                                       double *Gt, int slots, cudaStream_t s) {
+    return synthesis_t<double>(L, batch, pt, X, Gt, s, slots);
+}
+cudaError_t analysis_all_orders_slots(int L, int64_t batch, const double *pt, const double *U,
+                                      double *X, int slots, cudaStream_t s) {
+    return analysis_t<double>(L, batch, pt, U, X, s, slots);
 }
 
 }  // namespace sht

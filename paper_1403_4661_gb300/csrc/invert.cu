@@ -10,11 +10,11 @@ namespace {
 
 constexpr int kThreads = 512;
 
-__global__ void __launch_bounds__(kThreads) k_gauss_jordan(int L, const double *__restrict__ pt,
+__global__ void __launch_bounds__(kThreads) k_gauss_jordan(int L, int m_first, const double *__restrict__ pt,
                                                            double *__restrict__ pinv,
                                                            int *__restrict__ status) {
     extern __shared__ double sm[];
-    const int m = blockIdx.x;
+    const int m = m_first + (int)blockIdx.x;
     const int n = L - m;
     double *f = sm;               // column j of the rows, before elimination
     double *rowj = sm + n;        // pivot row after scaling
@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(kThreads) k_gauss_jordan(int L, const double *
 
 }  // namespace
 
-cudaError_t build_inverses(int L, const double *d_pt, double *d_pinv, cudaStream_t s) {
+cudaError_t build_inverses(int L, const double *d_pt, double *d_pinv, cudaStream_t s, int m_first) {
+    if (m_first >= L) return cudaSuccess;
     int *status = nullptr;
     cudaError_t e = cudaMallocAsync((void **)&status, sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -109,7 +110,7 @@ cudaError_t build_inverses(int L, const double *d_pt, double *d_pinv, cudaStream
     size_t smem = sizeof(double) * 2 * (size_t)L + sizeof(int) * (size_t)L;
     e = cudaFuncSetAttribute(k_gauss_jordan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) { cudaFreeAsync(status, s); return e; }
-    k_gauss_jordan<<<L, kThreads, smem, s>>>(L, d_pt, d_pinv, status);
+    k_gauss_jordan<<<L - m_first, kThreads, smem, s>>>(L, m_first, d_pt, d_pinv, status);
     e = cudaGetLastError();
     int h = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -114,6 +114,12 @@ __global__ void __launch_bounds__(128) k_table(int L, const double *__restrict__
 
 }  // namespace
 
+cudaError_t sectoral_values(int L, const double *d_theta_rows, int nrows, double *mant, int *expo,
+                            cudaStream_t s) {
+    k_sectoral<<<(nrows + 127) / 128, 128, 0, s>>>(L, d_theta_rows, nrows, mant, expo);
+    return cudaGetLastError();
+}
+
 cudaError_t build_ptilde_table(int L, const double *d_theta_rows, int nrows, double *d_table,
                                cudaStream_t s) {
     double *mant = nullptr;

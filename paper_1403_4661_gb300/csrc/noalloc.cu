@@ -111,6 +111,7 @@ extern "C" sht_status sht_forward_noalloc(sht_plan_t p, const void *d_samples, v
     if (st != SHT_OK) return st;
     if (p->dtype == SHT_F32)
         return set_error(SHT_ERR_UNSUPPORTED, "sht_forward_noalloc: complex128 plans only (not SHT_F32)");
+    if (p->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "sht_forward_noalloc: scalar (spin-0) plans only");
     if (batch == 0) return SHT_OK;
     const int L = p->L;
 

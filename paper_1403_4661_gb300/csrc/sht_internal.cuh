@@ -109,8 +109,11 @@ struct sht_plan_s {
     int device = 0;
     std::vector<double> theta;
     double *d_theta = nullptr;
-    double *pt = nullptr;       // P~ table
-    double *pinv = nullptr;     // per-order inverses
+    double *pt = nullptr;       // P~ table (spin plans: sP~^{+m})
+    double *pinv = nullptr;     // per-order inverses (spin plans: of the +m matrices)
+    int spin = 0;               // spin weight s of the plan's signals (Sec. III-H); 0: scalar
+    double *pt2 = nullptr;      // spin plans: (-1)^m sP~^{-m}, layout of pt
+    double *pinv2 = nullptr;    // spin plans: inverses of the -m matrices, layout of pinv
     float *ptF = nullptr;       // SHT_F32: the P~ table rounded to float32
     float *pinvF = nullptr;     // SHT_F32: the per-order inverses rounded to float32
     sht::DftPlan dft;
@@ -169,9 +172,23 @@ sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch
 cudaError_t build_ptilde_table(int L, const double *d_theta_rows, int nrows, double *d_table,
                                cudaStream_t s);
 // Table layout for nrows != L: block m at nrows * rows_off(L, m), nrows x n_m.
+// The sectoral values P~_m^m(theta_r) = mant[m * nrows + r] * 2^expo[m * nrows + r], m < L.
+cudaError_t sectoral_values(int L, const double *d_theta_rows, int nrows, double *mant, int *expo,
+                            cudaStream_t s);
 
-// invert.cu: explicit inverses of P_m for every m from the P~ table.
-cudaError_t build_inverses(int L, const double *d_pt, double *d_pinv, cudaStream_t s);
+// invert.cu: explicit inverses of P_m for every m >= m_first from the P~ table (blocks of
+// orders below m_first are left as they are).
+cudaError_t build_inverses(int L, const double *d_pt, double *d_pinv, cudaStream_t s, int m_first = 0);
+
+// spin.cu: spin-s tables (pt: sP~^{+m}, pt2: (-1)^m sP~^{-m}; scalar P~ layout) and per-order
+// (pseudo-)inverses; `singular` is set when a square P_m is singular for these co-latitudes.
+cudaError_t build_spin_tables(int L, int spin, const double *d_theta, double *pt, double *pt2,
+                              double *pinv, double *pinv2, bool &singular, cudaStream_t s);
+// spin-s transforms on the float64 SIMT kernels (workspaces of p->ws)
+cudaError_t spin_forward(sht_plan_t p, const double2 *d_samples, double2 *d_coeffs, int64_t batch, cudaStream_t s);
+cudaError_t spin_inverse(sht_plan_t p, const double2 *d_coeffs, double2 *d_samples, int64_t batch, cudaStream_t s);
+cudaError_t spin_inverse_adjoint(sht_plan_t p, const double2 *d_samples, double2 *d_coeffs, int64_t batch,
+                                 cudaStream_t s);
 
 // dft.cu
 cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s);
@@ -219,6 +236,7 @@ struct GemmArgsT {
     int64_t part_cap = 0;  // elements available at part
     int split_cap = 0;     // most K-splits per product (0: the launcher's default, 16)
     int64_t *launches = nullptr;  // incremented by the number of kernels launched
+    int slots = 3;         // epilogue column pairs written (bit 0: +m, bit 1: -m; spin plans)
 };
 using GemmArgs = GemmArgsT<double>;
 // Single problem: C[M x N] (+)= op(A)[M x K] * B[K x N], row-major, N = 4 * batch.
@@ -237,6 +255,11 @@ cudaError_t analysis_all_orders(int L, int64_t batch, const double *pt, const do
                                 double *X, cudaStream_t s);
 cudaError_t synthesis_all_orders(int L, int64_t batch, const float *pt, const float *X,
                                  float *Gt, cudaStream_t s);
+// The float64 grouped contractions writing only the column pairs in `slots` (spin plans).
+cudaError_t synthesis_all_orders_slots(int L, int64_t batch, const double *pt, const double *X,
+                                       double *Gt, int slots, cudaStream_t s);
+cudaError_t analysis_all_orders_slots(int L, int64_t batch, const double *pt, const double *U,
+                                      double *X, int slots, cudaStream_t s);
 cudaError_t analysis_all_orders(int L, int64_t batch, const float *pt, const float *U,
                                 float *X, cudaStream_t s);
 

@@ -38,7 +38,8 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_last_error_message", "sht_plan_set_timing", "sht_plan_stage_times",
             "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement",
             "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit",
-            "sht_plan_set_paths", "sht_plan_autotune", "sht_plan_save", "sht_plan_load"]
+            "sht_plan_set_paths", "sht_plan_autotune", "sht_plan_save", "sht_plan_load",
+            "sht_plan_spin", "sht_plan_spin_with_thetas"]
 SHT_PATH_DEFAULT = 0
 SHT_PATH_TENSOR = 1
 SHT_PATH_SIMT = 2
@@ -57,7 +58,7 @@ class ShtInfo(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_uint64), ("workspace_batch", ctypes.c_int64),
                 ("plan_seconds", ctypes.c_double), ("order_seconds", ctypes.c_double),
                 ("kernel_launches", ctypes.c_int64), ("refine_iterations", ctypes.c_int),
-                ("refine_last_update", ctypes.c_double)]
+                ("refine_last_update", ctypes.c_double), ("spin", ctypes.c_int)]
 
 
 class ShtTuning(ctypes.Structure):
@@ -82,6 +83,9 @@ def load_library(path=LIB_PATH):
     lib.sht_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(P)]
     lib.sht_plan_with_thetas.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_uint32, ctypes.POINTER(P)]
+    lib.sht_plan_spin.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(P)]
+    lib.sht_plan_spin_with_thetas.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_double), ctypes.c_uint32, ctypes.POINTER(P)]
     lib.sht_plan_thetas.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.sht_plan_bandlimit.argtypes = [P]
     lib.sht_plan_bandlimit.restype = ctypes.c_int
@@ -145,6 +149,25 @@ def sht_plan_with_thetas(L, theta, dtype=SHT_F64, flags=0):
     _check(lib.sht_plan_with_thetas(int(L), int(dtype),
                                     th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     int(flags), ctypes.byref(h)))
+    return h
+
+
+def sht_plan_spin(L, spin, dtype=SHT_F64, flags=SHT_ORDER_GREEDY):
+    lib = load_library()
+    h = ctypes.c_void_p()
+    _check(lib.sht_plan_spin(int(L), int(spin), int(dtype), int(flags), ctypes.byref(h)))
+    return h
+
+
+def sht_plan_spin_with_thetas(L, spin, theta, dtype=SHT_F64, flags=0):
+    lib = load_library()
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    if th.shape != (L,):
+        raise ValueError("theta must have L entries")
+    h = ctypes.c_void_p()
+    _check(lib.sht_plan_spin_with_thetas(int(L), int(spin), int(dtype),
+                                         th.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         int(flags), ctypes.byref(h)))
     return h
 
 
@@ -283,18 +306,23 @@ class Plan:
     Plan(L, ordering="simple")        the ordering of Eq. (20)
     Plan(L, measure="sin" | "tan13")  rings from the sets of the alternative measures (Sec. III-F)
     Plan(L, theta=array_of_L_values)  caller-given ring co-latitudes
+    Plan(L, spin=s)                   spin-s functions (Sec. III-H), float64 only
     """
 
-    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64, measure="uniform"):
+    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64, measure="uniform", spin=0):
         self.L = int(L)
         dtype = DTYPES.get(dtype, dtype)
         self.dtype = dtype
+        self.spin = int(spin)
         # element type of the plan's signals: complex64 for SHT_F32, complex128 otherwise
         self.cdtype = torch.complex64 if dtype == SHT_F32 else torch.complex128
-        if theta is not None:
+        flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering] | MEASURES[measure]
+        if self.spin != 0:
+            self.handle = (sht_plan_spin_with_thetas(self.L, self.spin, theta, dtype) if theta is not None
+                           else sht_plan_spin(self.L, self.spin, dtype, flags))
+        elif theta is not None:
             self.handle = sht_plan_with_thetas(self.L, theta, dtype)
         else:
-            flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering] | MEASURES[measure]
             self.handle = sht_plan(self.L, dtype, flags)
         self.theta = sht_plan_thetas(self.handle, self.L)
 
