@@ -449,8 +449,8 @@ def _synthesis_flops(L, B):
 
 def _ring_dft_flops(L, B):
     """float64 flops of one direction's ring DFTs, by the ring classes of csrc/dft.cu: direct
-    rings (N <= 63) 8 N^2; chirp-z rings two FFTs of the ring's convolution length M
-    (5 M log2 M each, the radix-2 count) plus the chirp and filter products (6 M + 12 N)."""
+    rings (N <= 63) 8 N^2; chirp-z rings two FFTs of the ring's convolution length M (the
+    nominal 5 M log2 M each) plus the chirp and filter products (6 M + 12 N)."""
     tot = 0.0
     for k in range(L):
         N = 2 * k + 1
@@ -463,10 +463,16 @@ def _ring_dft_flops(L, B):
 
 
 def _bluestein_length(N):
-    """Convolution length of a chirp-z ring of length N, as chosen in csrc/dft.cu."""
-    k = (N - 1) // 2
-    j = int(math.floor(math.log2(k)))
-    return 1 << (j + 3)
+    """Convolution length of a chirp-z ring of length N, as csrc/dft.cu chooses it: the smallest
+    2^a or 3 * 2^a that is at least 2N - 1."""
+    best = None
+    for a in range(4, 30):
+        p2, p3 = 1 << a, 3 << (a - 1)
+        if p3 >= 2 * N - 1 and p3 >= 16:
+            best = p3 if best is None else min(best, p3)
+        if p2 >= 2 * N - 1:
+            return p2 if best is None else min(best, p2)
+    return best
 
 
 def _src_hash(name):

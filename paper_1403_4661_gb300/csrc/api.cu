@@ -274,13 +274,6 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
     return SHT_OK;
 }
 
-// Number of ring-DFT launches per transform: direct rings, then one per chirp-z length class.
-int64_t ring_launches(int L) {
-    int64_t n = 1;
-    for (int j = 5; (1 << j) < L; ++j) ++n;
-    return n;
-}
-
 cudaEvent_t take_event(sht_plan_t p) {
     if (!p->ev_pool.empty()) {
         cudaEvent_t e = p->ev_pool.back();
@@ -375,7 +368,7 @@ cudaError_t forward_f32(sht_plan_t p, Workspace &w, const float2 *d_samples, flo
         Span sp(p, SHT_STAGE_RING_DFT, s);
         e = ring_dft_to_bins(p->L, p->dft, d_samples, W, batch, true, s);
     }
-    p->launches += ring_launches(p->L);
+    p->launches += dft_launches(p->dft);
     if (e == cudaSuccess) e = simt_chain<float>(p, w, W, d_coeffs, batch, s);
     return e;
 }
@@ -399,7 +392,7 @@ cudaError_t simt_inverse(sht_plan_t p, Workspace &w, const cplx_t<T> *d_coeffs, 
         Span sp(p, SHT_STAGE_RING_IDFT, s);
         e = fold_ring_idft(L, p->dft, G, d_samples, batch, s);
     }
-    p->launches += 2 + ring_launches(L);
+    p->launches += 2 + dft_launches(p->dft);
     return e;
 }
 
@@ -423,7 +416,7 @@ cudaError_t simt_inverse_adjoint(sht_plan_t p, const cplx_t<T> *d_samples, cplx_
         Span sp(p, SHT_STAGE_LAYOUT, s);
         e = orders_to_coeffs(L, batch, X, d_coeffs, s);
     }
-    p->launches += 2 + ring_launches(L);
+    p->launches += 2 + dft_launches(p->dft);
     return e;
 }
 
@@ -465,7 +458,7 @@ cudaError_t simt_forward_adjoint(sht_plan_t p, const cplx_t<T> *d_coeffs, cplx_t
         Span sp(p, SHT_STAGE_RING_IDFT, s);
         e = bins_to_ring_adjoint(L, p->dft, W, d_samples, batch, s);
     }
-    p->launches += 1 + (L - 1) + ring_launches(L);  // layout, alias gathers, ring DFTs
+    p->launches += 1 + (L - 1) + dft_launches(p->dft);  // layout, alias gathers, ring DFTs
     return e;
 }
 
@@ -481,7 +474,7 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         Span sp(p, SHT_STAGE_RING_DFT, s);
         e = ring_dft_to_bins(L, p->dft, d_samples, W, batch, true, s);
     }
-    p->launches += ring_launches(L);
+    p->launches += dft_launches(p->dft);
     const sht_tuning *tu = tuning_for(p, batch);
     const bool simt = !tensor_plan(p) || (nsl == kTcSlices && tu && tu->forward_path == SHT_PATH_SIMT);
     if (!simt) {
@@ -524,7 +517,7 @@ cudaError_t inverse_impl(sht_plan_t p, Workspace &w, const double2 *d_coeffs, do
         Span sp(p, SHT_STAGE_RING_IDFT, s);
         e = fold_ring_idft(L, p->dft, w.g, d_samples, batch, s);
     }
-    p->launches += 2 + ring_launches(L);
+    p->launches += 2 + dft_launches(p->dft);
     return e;
 }
 

@@ -10,13 +10,25 @@
 // DFT of length N_k per ring finishes the sum.
 //
 // Ring lengths are odd and often prime.  Rings with N <= kDirectMaxN are transformed directly
-// (O(N^2), twiddles from a per-ring table of N roots).  Longer rings use Bluestein's chirp-z
-// identity  j n = (j^2 + n^2 - (j - n)^2) / 2: with c_n = e^{-i pi n^2 / N},
+// (O(N^2)).  Longer rings use Bluestein's chirp-z identity  j n = (j^2 + n^2 - (j - n)^2) / 2:
+// with c_n = e^{-i pi n^2 / N},
 //     X_j = c_j sum_n (x_n c_n) conj(c_{j-n}),
-// a linear convolution computed as a cyclic one of power-of-two length M >= 2N - 1 with a radix-2
-// FFT held in shared memory (one thread block per ring and signal).  c_n is evaluated from the
-// exactly reduced integer n^2 mod 2N, so no twiddle carries an argument-reduction error.
-// Rings are launched in classes k in [2^j, 2^(j+1)), which share M = 2^(j+3).
+// a linear convolution computed as a cyclic one of length M >= 2N - 1, the smallest M of the
+// form 2^a or 3 * 2^a (c_n is evaluated from the exactly reduced integer n^2 mod 2N).  On GB300
+// these kernels are bound by the float64 pipe (one FP64 instruction per 64 cycles per scheduler;
+// an add costs as much as an FMA), so the design minimises float64 instructions:
+//   * the forward FFT is decimation-in-frequency (natural order in, digit-reversed order out),
+//     the filter FFT(conj c) is stored in that digit-reversed order, and the inverse FFT is the
+//     matching decimation-in-time network (digit-reversed in, natural out): no permutation pass;
+//   * radix-4 stages, then a radix-2 and / or radix-3 stage (3 * 2^a lengths cut M by up to 25 %);
+//   * the input holds N <= M/2 values, so the first stage's radix-4 butterflies have two zero
+//     inputs; only N <= M/2 outputs are needed, so the last stage computes two of its four;
+//   * the chirp premultiply and the fold (or sample load) are fused into the first stage, the
+//     filter product into the last forward stage, the chirp postmultiply and the output layout
+//     into the last inverse stage; one __syncthreads per stage, data in shared memory.
+// Rings are launched in classes of consecutive k sharing M.
+#include <algorithm>
+
 #include "sht_internal.cuh"
 
 namespace sht {
@@ -28,73 +40,230 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
+// a * conj(b)
+__device__ __forceinline__ double2 cmulc(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
 template <typename C> __device__ __forceinline__ C conjd(C a) { a.y = -a.y; return a; }
 template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+// -i a and +i a
+template <typename C> __device__ __forceinline__ C mul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+template <typename C> __device__ __forceinline__ C mul_pi(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
 __device__ __forceinline__ void sincospi_t(double x, double *s, double *c) { sincospi(x, s, c); }
 __device__ __forceinline__ void sincospi_t(float x, float *s, float *c) { sincospif(x, s, c); }
 
-// In-place decimation-in-time FFT of a[0..M) in shared memory, natural-order input and output:
-// bit-reversal permutation, then the radix-2 stages taken two at a time as radix-4 butterflies
-// (stages s, s+1 with half-width h share the twiddle u = W_{4h}^j: the four outputs need u x2,
-// u^2 x1, u^3 x3 and the factor W_{4h}^h = -i, i.e. 3 complex products instead of 4), plus one
-// radix-2 stage of twiddle 1 when log2 M is odd.  tw[t] = e^{-2 pi i t / Mmax}, t < Mmax;
-// inverse = conjugate twiddles, unnormalised.
+constexpr int kMaxStages = 10;
+constexpr int kThreads = 256;
+
+// Radices of one convolution length M, in decimation-in-frequency order: 4, .., 4, then 2 when
+// log2 of the power-of-two part is odd, then 3 for M = 3 * 2^a.  st.S[s] is the sub-transform
+// length entering stage s (S[0] = M).
+struct Stages {
+    int n;
+    int R[kMaxStages];
+    int S[kMaxStages];
+};
+
+Stages stages_of(int M) {
+    Stages st{};
+    int p = M, three = 0;
+    if (p % 3 == 0) { three = 1; p /= 3; }
+    int a = 0;
+    while ((1 << a) < p) ++a;
+    for (int i = 0; i < a / 2; ++i) st.R[st.n++] = 4;
+    if (a & 1) st.R[st.n++] = 2;
+    if (three) st.R[st.n++] = 3;
+    int S = M;
+    for (int s = 0; s < st.n; ++s) { st.S[s] = S; S /= st.R[s]; }
+    return st;
+}
+
+// Smallest 2^a or 3 * 2^a >= 2N - 1 (and >= 16).
+int bluestein_length(int N) {
+    int best = 1 << 30;
+    for (int a = 4; a < 30; ++a) {
+        const int p2 = 1 << a, p3 = 3 << (a - 1);
+        if (p3 >= 2 * N - 1 && p3 >= 16) best = std::min(best, p3);
+        if (p2 >= 2 * N - 1) { best = std::min(best, p2); break; }
+    }
+    return best;
+}
+
+// sin(2 pi / 3)
+template <typename T> __device__ __forceinline__ T sin60() { return (T)0.86602540378443864676372317075293618; }
+
+// ---- decimation-in-frequency stage s (forward FFT), in place -------------------------------
+// Block of length S = R S': for j < S', inputs a_q = x[o + j + q S'], outputs
+// y_p = DFT_R(a)_p * w_S^{p j} at o + j + p S' (w_S = e^{-2 pi i / S}, tw[t] = w_Mtab^t).
 template <typename C>
-__device__ void block_fft(C *a, int M, int logM, const C *__restrict__ tw, int Mmax, bool inverse) {
-    for (int i = threadIdx.x; i < M; i += blockDim.x) {
-        int j = (int)(__brev((unsigned)i) >> (32 - logM));
-        if (i < j) { C t = a[i]; a[i] = a[j]; a[j] = t; }
-    }
-    __syncthreads();
-    int s = 1;
-    if (logM & 1) {
-        for (int t = threadIdx.x; t < (M >> 1); t += blockDim.x) {
-            const C u = a[2 * t], v = a[2 * t + 1];
-            a[2 * t] = cadd(u, v);
-            a[2 * t + 1] = csub(u, v);
-        }
-        __syncthreads();
-        s = 2;
-    }
-    for (; s < logM; s += 2) {
-        const int h = 1 << (s - 1);
-        const int stride = Mmax >> (s + 1);   // u = W_{4h}^j = tw[j * stride]
-        for (int t = threadIdx.x; t < (M >> 2); t += blockDim.x) {
-            const int j = t & (h - 1);
-            const int i0 = ((t >> (s - 1)) << (s + 1)) + j;
-            const C x0 = a[i0], x1 = a[i0 + h], x2 = a[i0 + 2 * h], x3 = a[i0 + 3 * h];
-            C t1 = x1, t2 = x2, t3 = x3;
-            if (h > 1) {   // h == 1: j == 0, every twiddle is 1
-                C u = __ldg(&tw[j * stride]), u2 = __ldg(&tw[2 * j * stride]), u3 = __ldg(&tw[3 * j * stride]);
-                if (inverse) { u.y = -u.y; u2.y = -u2.y; u3.y = -u3.y; }
-                t1 = cmul(x1, u2);
-                t2 = cmul(x2, u);
-                t3 = cmul(x3, u3);
+__device__ __forceinline__ void dif_stage(C *a, int M, int S, int R, const C *__restrict__ tw, int Mtab,
+                                          const C *__restrict__ filt) {
+    const int Sp = S / R, nb = M / R, ts = Mtab / S;
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        const int blk = idx / Sp, j = idx - blk * Sp;
+        C *p = a + blk * S + j;
+        if (R == 4) {
+            C a0 = p[0], a1 = p[Sp], a2 = p[2 * Sp], a3 = p[3 * Sp];
+            const C A = cadd(a0, a2), Bm = csub(a0, a2), Cc = cadd(a1, a3), D = csub(a1, a3);
+            a0 = cadd(A, Cc);
+            a2 = csub(A, Cc);
+            a1 = cadd(Bm, mul_mi(D));
+            a3 = csub(Bm, mul_mi(D));
+            if (j) {
+                a1 = cmul(a1, __ldg(&tw[j * ts]));
+                a2 = cmul(a2, __ldg(&tw[2 * j * ts]));
+                a3 = cmul(a3, __ldg(&tw[3 * j * ts]));
             }
-            const C A = cadd(x0, t1), Bm = csub(x0, t1), Cs = cadd(t2, t3), D = csub(t2, t3);
-            a[i0] = cadd(A, Cs);
-            a[i0 + 2 * h] = csub(A, Cs);
-            C o1 = Bm, o3 = Bm;
-            if (!inverse) {   // W_{4h}^h = -i
-                o1.x += D.y; o1.y -= D.x;
-                o3.x -= D.y; o3.y += D.x;
-            } else {          // +i
-                o1.x -= D.y; o1.y += D.x;
-                o3.x += D.y; o3.y -= D.x;
+            if (filt) {
+                const int o = blk * S + j;
+                a0 = cmul(a0, __ldg(&filt[o])); a1 = cmul(a1, __ldg(&filt[o + Sp]));
+                a2 = cmul(a2, __ldg(&filt[o + 2 * Sp])); a3 = cmul(a3, __ldg(&filt[o + 3 * Sp]));
             }
-            a[i0 + h] = o1;
-            a[i0 + 3 * h] = o3;
+            p[0] = a0; p[Sp] = a1; p[2 * Sp] = a2; p[3 * Sp] = a3;
+        } else if (R == 2) {
+            C a0 = p[0], a1 = p[Sp];
+            const C s0 = cadd(a0, a1);
+            C s1 = csub(a0, a1);
+            if (j) s1 = cmul(s1, __ldg(&tw[j * ts]));
+            if (filt) {
+                const int o = blk * S + j;
+                p[0] = cmul(s0, __ldg(&filt[o])); p[Sp] = cmul(s1, __ldg(&filt[o + Sp]));
+            } else {
+                p[0] = s0; p[Sp] = s1;
+            }
+        } else {   // R == 3: y0 = a0 + t1, y1,2 = a0 - t1/2 -+ i sin60 (a1 - a2), t1 = a1 + a2
+            using T = decltype(a[0].x);
+            const C a0 = p[0], a1 = p[Sp], a2 = p[2 * Sp];
+            const C t1 = cadd(a1, a2);
+            C t2;
+            t2.x = fma((T)-0.5, t1.x, a0.x);
+            t2.y = fma((T)-0.5, t1.y, a0.y);
+            C d = csub(a1, a2);
+            d.x *= sin60<T>();
+            d.y *= sin60<T>();
+            C y0 = cadd(a0, t1), y1 = cadd(t2, mul_mi(d)), y2 = csub(t2, mul_mi(d));
+            if (j) {
+                y1 = cmul(y1, __ldg(&tw[j * ts]));
+                y2 = cmul(y2, __ldg(&tw[2 * j * ts]));
+            }
+            if (filt) {
+                const int o = blk * S + j;
+                y0 = cmul(y0, __ldg(&filt[o])); y1 = cmul(y1, __ldg(&filt[o + Sp]));
+                y2 = cmul(y2, __ldg(&filt[o + 2 * Sp]));
+            }
+            p[0] = y0; p[Sp] = y1; p[2 * Sp] = y2;
         }
-        __syncthreads();
     }
 }
 
-__global__ void k_twiddle(double2 *tw, int Mmax) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= Mmax) return;
+// ---- decimation-in-time stage s (inverse FFT, unnormalised), in place ------------------------
+// The inverse of dif_stage: b_p = y[o + j + p S'] * conj(w_S^{p j}), x_q = sum_p b_p e^{+2 pi i pq/R}.
+template <typename C>
+__device__ __forceinline__ void dit_stage(C *a, int M, int S, int R, const C *__restrict__ tw, int Mtab) {
+    const int Sp = S / R, nb = M / R, ts = Mtab / S;
+    for (int idx = threadIdx.x; idx < nb; idx += blockDim.x) {
+        const int blk = idx / Sp, j = idx - blk * Sp;
+        C *p = a + blk * S + j;
+        if (R == 4) {
+            C b0 = p[0], b1 = p[Sp], b2 = p[2 * Sp], b3 = p[3 * Sp];
+            if (j) {
+                b1 = cmulc(b1, __ldg(&tw[j * ts]));
+                b2 = cmulc(b2, __ldg(&tw[2 * j * ts]));
+                b3 = cmulc(b3, __ldg(&tw[3 * j * ts]));
+            }
+            const C A = cadd(b0, b2), Bm = csub(b0, b2), Cc = cadd(b1, b3), D = csub(b1, b3);
+            p[0] = cadd(A, Cc);
+            p[2 * Sp] = csub(A, Cc);
+            p[Sp] = cadd(Bm, mul_pi(D));
+            p[3 * Sp] = csub(Bm, mul_pi(D));
+        } else if (R == 2) {
+            C b0 = p[0], b1 = p[Sp];
+            if (j) b1 = cmulc(b1, __ldg(&tw[j * ts]));
+            p[0] = cadd(b0, b1);
+            p[Sp] = csub(b0, b1);
+        } else {
+            using T = decltype(a[0].x);
+            C b0 = p[0], b1 = p[Sp], b2 = p[2 * Sp];
+            if (j) {
+                b1 = cmulc(b1, __ldg(&tw[j * ts]));
+                b2 = cmulc(b2, __ldg(&tw[2 * j * ts]));
+            }
+            const C t1 = cadd(b1, b2);
+            C t2;
+            t2.x = fma((T)-0.5, t1.x, b0.x);
+            t2.y = fma((T)-0.5, t1.y, b0.y);
+            C d = csub(b1, b2);
+            d.x *= sin60<T>();
+            d.y *= sin60<T>();
+            p[0] = cadd(b0, t1);
+            p[Sp] = cadd(t2, mul_pi(d));
+            p[2 * Sp] = csub(t2, mul_pi(d));
+        }
+    }
+}
+
+// Bluestein convolution of one ring: X_t = c_t sum_n (x_n c_n) conj(c_{t-n}), t < N, with
+// x_n = in(n) (n < N) and out(t, X_t) for t < N.  a: M complex values of shared memory.
+template <typename C, typename In, typename Out>
+__device__ __forceinline__ void bluestein(C *a, int N, int M, const Stages &st, const C *__restrict__ tw, int Mtab,
+                                          const C *__restrict__ chirp, const C *__restrict__ filt, In in, Out out) {
+    // first forward stage (R = 4, S = M) with the chirp premultiply; inputs j + 2M/4, j + 3M/4 are
+    // beyond N <= M/2, input j + M/4 is beyond N for j >= N - M/4
+    {
+        const int Q = M >> 2, ts = Mtab / M;
+        for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+            const C a0 = cmul(in(j), __ldg(&chirp[j]));
+            C a1;
+            if (j + Q < N) a1 = cmul(in(j + Q), __ldg(&chirp[j + Q]));
+            else { a1.x = 0; a1.y = 0; }
+            C y0 = cadd(a0, a1), y1 = cadd(a0, mul_mi(a1)), y2 = csub(a0, a1), y3 = csub(a0, mul_mi(a1));
+            if (j) {
+                y1 = cmul(y1, __ldg(&tw[j * ts]));
+                y2 = cmul(y2, __ldg(&tw[2 * j * ts]));
+                y3 = cmul(y3, __ldg(&tw[3 * j * ts]));
+            }
+            if (st.n == 1) {
+                y0 = cmul(y0, __ldg(&filt[j])); y1 = cmul(y1, __ldg(&filt[j + Q]));
+                y2 = cmul(y2, __ldg(&filt[j + 2 * Q])); y3 = cmul(y3, __ldg(&filt[j + 3 * Q]));
+            }
+            a[j] = y0; a[j + Q] = y1; a[j + 2 * Q] = y2; a[j + 3 * Q] = y3;
+        }
+        __syncthreads();
+    }
+    for (int s = 1; s < st.n; ++s) {
+        dif_stage(a, M, st.S[s], st.R[s], tw, Mtab, s == st.n - 1 ? filt : (const C *)nullptr);
+        __syncthreads();
+    }
+    for (int s = st.n - 1; s >= 1; --s) {
+        dit_stage(a, M, st.S[s], st.R[s], tw, Mtab);
+        __syncthreads();
+    }
+    // last inverse stage (R = 4, S = M): outputs j and j + M/4 only (the others are >= M/2 >= N),
+    // with the chirp postmultiply
+    {
+        const int Q = M >> 2, ts = Mtab / M;
+        for (int j = threadIdx.x; j < Q; j += blockDim.x) {
+            C b0 = a[j], b1 = a[j + Q], b2 = a[j + 2 * Q], b3 = a[j + 3 * Q];
+            if (j) {
+                b1 = cmulc(b1, __ldg(&tw[j * ts]));
+                b2 = cmulc(b2, __ldg(&tw[2 * j * ts]));
+                b3 = cmulc(b3, __ldg(&tw[3 * j * ts]));
+            }
+            out(j, cmul(cadd(cadd(b0, b2), cadd(b1, b3)), __ldg(&chirp[j])));
+            if (j + Q < N) out(j + Q, cmul(cadd(csub(b0, b2), mul_pi(csub(b1, b3))), __ldg(&chirp[j + Q])));
+        }
+    }
+}
+
+__global__ void k_twiddle(double2 *tw, int Mtab) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= Mtab) return;
     double s, c;
-    sincospi(2.0 * (double)t / (double)Mmax, &s, &c);
+    sincospi(2.0 * (double)t / (double)Mtab, &s, &c);
     tw[t] = make_double2(c, -s);
 }
 
@@ -117,26 +286,29 @@ __global__ void k_to_f32c(const double2 *__restrict__ in, float2 *__restrict__ o
     if (t < n) out[t] = make_float2((float)in[t].x, (float)in[t].y);
 }
 
-// Filter of ring k: FFT_M of b_t = conj(c_t) (t < N), b_{M-t} = conj(c_t) (0 < t < N), scaled 1/M.
-__global__ void k_filter(int k0, const double2 *__restrict__ chirp, const int64_t *__restrict__ foff,
-                         const int *__restrict__ fM, const double2 *__restrict__ tw, int Mmax,
-                         double2 *__restrict__ filt) {
-    extern __shared__ double2 sa[];
+// Filter of ring k0 + blockIdx.x, stored in the forward FFT's (digit-reversed) output order:
+// DIF-FFT_M of b_t = conj(c_t) (t < N), b_{M-t} = conj(c_t) (0 < t < N), scaled 1/M.
+__global__ void k_filter(int k0, int M, Stages st, const double2 *__restrict__ chirp, const double2 *__restrict__ tw,
+                         int Mtab, double2 *__restrict__ filt) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *a = reinterpret_cast<double2 *>(smem_raw);
     const int k = k0 + blockIdx.x;
-    const int N = 2 * k + 1, M = fM[k];
-    int logM = 31 - __clz(M);
+    const int N = 2 * k + 1;
     const double2 *c = chirp + (int64_t)k * k;
     for (int t = threadIdx.x; t < M; t += blockDim.x) {
         double2 v = make_double2(0.0, 0.0);
         if (t < N) v = conjd(c[t]);
         else if (t > M - N) v = conjd(c[M - t]);
-        sa[t] = v;
+        a[t] = v;
     }
     __syncthreads();
-    block_fft(sa, M, logM, tw, Mmax, false);
+    for (int s = 0; s < st.n; ++s) {
+        dif_stage(a, M, st.S[s], st.R[s], tw, Mtab, (const double2 *)nullptr);
+        __syncthreads();
+    }
     const double sc = 1.0 / (double)M;
-    for (int t = threadIdx.x; t < M; t += blockDim.x)
-        filt[foff[k] + t] = make_double2(sa[t].x * sc, sa[t].y * sc);
+    double2 *f = filt + (int64_t)blockIdx.x * M;
+    for (int t = threadIdx.x; t < M; t += blockDim.x) f[t] = make_double2(a[t].x * sc, a[t].y * sc);
 }
 
 enum OutMode : int { OUT_BINS = 0, OUT_UNFOLD = 1 };
@@ -147,26 +319,89 @@ struct DftArgs {
     int L, k0;
     int64_t Nc;             // 4 * batch columns of the order-major buffers
     const cplx_t<T> *chirp, *filt, *tw;
-    const int64_t *foff;
-    int Mmax, M, logM;
+    int Mtab, M;            // M = 0: direct rings
+    Stages st;
 };
 
-// Forward DFT of ring k = k0 + blockIdx.x of signal b = blockIdx.y.
+// Store of one forward-transform value X_t (bin q = t or t - N) of ring k, signal b.
 //  OUT_BINS:   W rows of bins +-q (scaled 1/N)           - forward transform
-//  OUT_UNFOLD: Gt rows (|m|, k) for every |m| < L, value of bin alias_k(m) (unscaled)
+//  OUT_UNFOLD: Gt rows (|m|, k) for every |m| < L with m = q mod N (unscaled)
 //              - adjoint of fold_ring_idft
 template <typename T, int OUT>
-__global__ void k_ring_dft(DftArgs<T> d, const cplx_t<T> *__restrict__ samples, T *__restrict__ out) {
+__device__ __forceinline__ void store_bin(const DftArgs<T> &d, T *__restrict__ out, int k, int b, int t, cplx_t<T> v) {
+    const int N = 2 * k + 1, L = d.L;
+    const int q = (t <= k) ? t : t - N;
+    if (OUT == OUT_BINS) {
+        const T sc = (T)1 / (T)N;
+        const int o = q < 0 ? -q : q;
+        T *w = out + (rows_off(L, o) + (k - o)) * d.Nc + 4 * b;
+        if (q >= 0) { w[0] = v.x * sc; w[1] = v.y * sc; }
+        else        { w[2] = v.x * sc; w[3] = v.y * sc; }
+        if (q == 0) { w[2] = 0; w[3] = 0; }
+    } else {
+        // every order m = q + j N with |m| < L
+        int m = q - ((q + L - 1) / N) * N;
+        for (; m <= L - 1; m += N) {
+            const int o = m < 0 ? -m : m;
+            T *g = out + ((int64_t)o * L + k) * d.Nc + 4 * b;
+            if (m >= 0) { g[0] = v.x; g[1] = v.y; }
+            else        { g[2] = v.x; g[3] = v.y; }
+            if (m == 0) { g[2] = 0; g[3] = 0; }
+        }
+    }
+}
+
+// Bin value B_t of ring k, signal b, for the inverse direction.
+//  IN_FOLD: B_q = sum_{m = q mod N, |m| < L} Gt[(|m|, k)]             - inverse transform
+//  IN_BINS: B_q = W[bin q of ring k] / N                              - adjoint of the forward DFT
+template <typename T, int IN>
+__device__ __forceinline__ cplx_t<T> load_bin(const DftArgs<T> &d, const T *__restrict__ in, int k, int b, int t) {
+    const int N = 2 * k + 1, L = d.L;
+    const int q = (t <= k) ? t : t - N;
+    if (IN == IN_FOLD) {
+        // the orders of bin q, four loads in flight per step
+        const int m0 = q - ((q + L - 1) / N) * N;
+        T ax = 0, ay = 0;
+        int m = m0;
+        for (; m + 3 * N <= L - 1; m += 4 * N) {
+            T x[4], y[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int mm = m + u * N, o = mm < 0 ? -mm : mm;
+                const T *g = in + ((int64_t)o * L + k) * d.Nc + 4 * b + (mm < 0 ? 2 : 0);
+                x[u] = g[0];
+                y[u] = g[1];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) { ax += x[u]; ay += y[u]; }
+        }
+        for (; m <= L - 1; m += N) {
+            const int o = m < 0 ? -m : m;
+            const T *g = in + ((int64_t)o * L + k) * d.Nc + 4 * b + (m < 0 ? 2 : 0);
+            ax += g[0];
+            ay += g[1];
+        }
+        return mk2<T>(ax, ay);
+    } else {
+        const int o = q < 0 ? -q : q;
+        const T *w = in + (rows_off(L, o) + (k - o)) * d.Nc + 4 * b + (q < 0 ? 2 : 0);
+        const T sc = (T)1 / (T)N;
+        return mk2<T>(w[0] * sc, w[1] * sc);
+    }
+}
+
+// Forward DFT of ring k = k0 + blockIdx.x of signal b = blockIdx.y into the order-major layout.
+template <typename T, int OUT>
+__global__ void __launch_bounds__(kThreads) k_ring_dft(DftArgs<T> d, const cplx_t<T> *__restrict__ samples,
+                                                       T *__restrict__ out) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sa = reinterpret_cast<C *>(smem_raw);
     const int k = d.k0 + blockIdx.x, b = blockIdx.y, L = d.L;
     const int N = 2 * k + 1;
     const C *x = samples + (int64_t)b * L * L + (int64_t)k * k;
-    C *X;  // natural-order DFT, N values
     if (d.M == 0) {
         C *xs = sa, *roots = sa + N;
-        X = sa + 2 * N;
         for (int t = threadIdx.x; t < N; t += blockDim.x) {
             xs[t] = x[t];
             T s, c;
@@ -182,82 +417,67 @@ __global__ void k_ring_dft(DftArgs<T> d, const cplx_t<T> *__restrict__ samples, 
                 acc.x += p.x; acc.y += p.y;
                 idx += j; if (idx >= N) idx -= N;
             }
-            X[j] = acc;
+            store_bin<T, OUT>(d, out, k, b, j, acc);
         }
-        __syncthreads();
-    } else {
-        const C *c = d.chirp + (int64_t)k * k;
-        const C *f = d.filt + d.foff[k];
-        for (int t = threadIdx.x; t < d.M; t += blockDim.x)
-            sa[t] = (t < N) ? cmul(x[t], c[t]) : mk2<T>(0, 0);
-        __syncthreads();
-        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, false);
-        for (int t = threadIdx.x; t < d.M; t += blockDim.x) sa[t] = cmul(sa[t], f[t]);
-        __syncthreads();
-        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, true);
-        for (int t = threadIdx.x; t < N; t += blockDim.x) sa[t] = cmul(c[t], sa[t]);
-        __syncthreads();
-        X = sa;
+        return;
     }
-    if (OUT == OUT_BINS) {
-        const T sc = (T)1 / (T)N;
-        for (int j = threadIdx.x; j < N; j += blockDim.x) {
-            const int q = (j <= k) ? j : j - N;
-            const int o = q < 0 ? -q : q;
-            T *w = out + (rows_off(L, o) + (k - o)) * d.Nc + 4 * b;
-            C v = X[j];
-            if (q >= 0) { w[0] = v.x * sc; w[1] = v.y * sc; }
-            else        { w[2] = v.x * sc; w[3] = v.y * sc; }
-            if (q == 0) { w[2] = 0; w[3] = 0; }
-        }
-    } else {
-        for (int m = -(L - 1) + (int)threadIdx.x; m <= L - 1; m += blockDim.x) {
-            int q = alias_bin(m, k);
-            int j = q >= 0 ? q : q + N;
-            int o = m < 0 ? -m : m;
-            T *g = out + ((int64_t)o * L + k) * d.Nc + 4 * b;
-            C v = X[j];
-            if (m >= 0) { g[0] = v.x; g[1] = v.y; }
-            else        { g[2] = v.x; g[3] = v.y; }
-            if (m == 0) { g[2] = 0; g[3] = 0; }
-        }
-    }
+    const C *c = d.chirp + (int64_t)k * k;
+    const C *f = d.filt + (int64_t)blockIdx.x * d.M;
+    bluestein(sa, N, d.M, d.st, d.tw, d.Mtab, c, f,
+              [&](int t) { return x[t]; },
+              [&](int t, C v) { store_bin<T, OUT>(d, out, k, b, t, v); });
 }
 
-// Inverse DFT of ring k of signal b: gathers the ring's N bins, then s_n = sum_j B_j e^{+2 pi i jn/N}.
-//  IN_FOLD: B_q = sum_{m = q mod N, |m| < L} Gt[(|m|, k)]             - inverse transform
-//  IN_BINS: B_q = W[bin q of ring k] / N                              - adjoint of the forward DFT
+// Inverse DFT of ring k of signal b: s_n = sum_j B_j e^{+2 pi i jn/N} with the bins B of load_bin.
 template <typename T, int IN>
-__global__ void k_ring_idft(DftArgs<T> d, const T *__restrict__ in, cplx_t<T> *__restrict__ samples) {
+__global__ void __launch_bounds__(kThreads) k_ring_idft(DftArgs<T> d, const T *__restrict__ in,
+                                                        cplx_t<T> *__restrict__ samples) {
     using C = cplx_t<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *sa = reinterpret_cast<C *>(smem_raw);
     const int k = d.k0 + blockIdx.x, b = blockIdx.y, L = d.L;
     const int N = 2 * k + 1;
-    C *B = sa;  // natural-order bins
-    for (int j = threadIdx.x; j < N; j += blockDim.x) {
-        const int q = (j <= k) ? j : j - N;
-        C acc = mk2<T>(0, 0);
-        if (IN == IN_FOLD) {
-            int m = q - ((q + L - 1) / N) * N;
-            for (; m <= L - 1; m += N) {
-                const int o = m < 0 ? -m : m;
-                const T *g = in + ((int64_t)o * L + k) * d.Nc + 4 * b + (m < 0 ? 2 : 0);
-                acc.x += g[0];
-                acc.y += g[1];
-            }
-        } else {
-            const int o = q < 0 ? -q : q;
-            const T *w = in + (rows_off(L, o) + (k - o)) * d.Nc + 4 * b + (q < 0 ? 2 : 0);
-            const T sc = (T)1 / (T)N;
-            acc = mk2<T>(w[0] * sc, w[1] * sc);
-        }
-        B[j] = acc;
-    }
-    __syncthreads();
     C *y = samples + (int64_t)b * L * L + (int64_t)k * k;
     if (d.M == 0) {
-        C *roots = sa + N;
+        // direct ring: the N bins (each summed by a group of threads), then the direct sum
+        C *B = sa, *roots = sa + N, *part = sa + 2 * N;
+        if (IN == IN_FOLD) {
+            // bin q = t mod N, thread group g = t / N sums the orders of q with index = g mod G
+            const int G = max(1, (int)blockDim.x / N);
+            for (int t = threadIdx.x; t < N * G; t += blockDim.x) {
+                const int j = t % N, g = t / N;
+                const int q = (j <= k) ? j : j - N;
+                int m = q - ((q + L - 1) / N) * N + g * N;
+                T ax = 0, ay = 0;
+                for (; m + 3 * G * N <= L - 1; m += 4 * G * N) {
+                    T xv[4], yv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int mm = m + u * G * N, o = mm < 0 ? -mm : mm;
+                        const T *gp = in + ((int64_t)o * L + k) * d.Nc + 4 * b + (mm < 0 ? 2 : 0);
+                        xv[u] = gp[0];
+                        yv[u] = gp[1];
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { ax += xv[u]; ay += yv[u]; }
+                }
+                for (; m <= L - 1; m += G * N) {
+                    const int o = m < 0 ? -m : m;
+                    const T *gp = in + ((int64_t)o * L + k) * d.Nc + 4 * b + (m < 0 ? 2 : 0);
+                    ax += gp[0];
+                    ay += gp[1];
+                }
+                part[t] = mk2<T>(ax, ay);
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < N; j += blockDim.x) {
+                C acc = part[j];
+                for (int g = 1; g < G; ++g) acc = cadd(acc, part[g * N + j]);
+                B[j] = acc;
+            }
+        } else {
+            for (int j = threadIdx.x; j < N; j += blockDim.x) B[j] = load_bin<T, IN>(d, in, k, b, j);
+        }
         for (int t = threadIdx.x; t < N; t += blockDim.x) {
             T s, c;
             sincospi_t((T)2 * (T)t / (T)N, &s, &c);
@@ -274,48 +494,27 @@ __global__ void k_ring_idft(DftArgs<T> d, const T *__restrict__ in, cplx_t<T> *_
             }
             y[n] = acc;
         }
-    } else {
-        // y = conj(DFT(conj(B))) with the forward chirp machinery
-        const C *c = d.chirp + (int64_t)k * k;
-        const C *f = d.filt + d.foff[k];
-        for (int t = threadIdx.x; t < d.M; t += blockDim.x)
-            sa[t] = (t < N) ? cmul(conjd(sa[t]), c[t]) : mk2<T>(0, 0);
-        __syncthreads();
-        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, false);
-        for (int t = threadIdx.x; t < d.M; t += blockDim.x) sa[t] = cmul(sa[t], f[t]);
-        __syncthreads();
-        block_fft(sa, d.M, d.logM, d.tw, d.Mmax, true);
-        for (int t = threadIdx.x; t < N; t += blockDim.x) y[t] = conjd(cmul(c[t], sa[t]));
+        return;
     }
-}
-
-int ilog2(int x) { int r = 0; while ((1 << r) < x) ++r; return r; }
-
-// Ring classes: direct rings k < 32 (N <= 63), then k in [2^j, 2^(j+1)) with M = 2^(j+3).
-template <typename F>
-cudaError_t for_each_class(int L, F &&fn) {
-    int kd = L < 32 ? L : 32;
-    cudaError_t e = fn(0, kd, 0);
-    if (e != cudaSuccess) return e;
-    for (int j = 5; (1 << j) < L; ++j) {
-        int k0 = 1 << j, k1 = (1 << (j + 1)) < L ? (1 << (j + 1)) : L;
-        e = fn(k0, k1 - k0, 1 << (j + 3));
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    // y = conj(DFT(conj(B))) with the forward chirp machinery
+    const C *c = d.chirp + (int64_t)k * k;
+    const C *f = d.filt + (int64_t)blockIdx.x * d.M;
+    bluestein(sa, N, d.M, d.st, d.tw, d.Mtab, c, f,
+              [&](int t) { return conjd(load_bin<T, IN>(d, in, k, b, t)); },
+              [&](int t, C v) { y[t] = conjd(v); });
 }
 
 template <typename T>
-DftArgs<T> make_args(int L, const DftPlan &dp, int64_t batch, int k0, int M) {
+DftArgs<T> make_args(int L, const DftPlan &dp, int64_t batch, const RingClass &rc) {
     DftArgs<T> d{};
-    d.L = L; d.k0 = k0; d.Nc = 4 * batch;
+    d.L = L; d.k0 = rc.k0; d.Nc = 4 * batch;
     if constexpr (sizeof(T) == 8) {
-        d.chirp = dp.chirp; d.filt = dp.filt; d.tw = dp.twiddle;
+        d.chirp = dp.chirp; d.filt = dp.filt + rc.filt_off; d.tw = dp.twiddle;
     } else {
-        d.chirp = dp.chirp_f; d.filt = dp.filt_f; d.tw = dp.twiddle_f;
+        d.chirp = dp.chirp_f; d.filt = dp.filt_f + rc.filt_off; d.tw = dp.twiddle_f;
     }
-    d.foff = dp.filt_off;
-    d.Mmax = dp.Mmax; d.M = M; d.logM = M ? ilog2(M) : 0;
+    d.Mtab = dp.Mtab; d.M = rc.M;
+    d.st = rc.M ? stages_of(rc.M) : Stages{};
     return d;
 }
 
@@ -325,71 +524,74 @@ cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Shared memory of a class's blocks: M complex values (chirp-z), or the direct rings' bins,
+// roots and fold partials.
+template <typename T>
+size_t smem_bytes(const RingClass &rc) {
+    if (rc.M == 0) {
+        const int N = 2 * (rc.k0 + rc.cnt - 1) + 1;
+        return sizeof(cplx_t<T>) * ((size_t)2 * N + (size_t)std::max(N, kThreads));
+    }
+    return sizeof(cplx_t<T>) * (size_t)rc.M;
+}
+
 // Raise the dynamic shared-memory limit of the ring kernels once, at plan time, so that the
 // transform calls themselves make no attribute calls (they may run under stream capture).
 template <typename T>
 cudaError_t set_ring_kernel_limits_t(int Mmax) {
-    const size_t b = sizeof(cplx_t<T>) * (size_t)Mmax;
+    const size_t b = sizeof(cplx_t<T>) * (size_t)std::max(Mmax, 3 * 64);
     cudaError_t e;
     if ((e = set_smem(k_ring_dft<T, OUT_BINS>, b)) != cudaSuccess) return e;
     if ((e = set_smem(k_ring_dft<T, OUT_UNFOLD>, b)) != cudaSuccess) return e;
     if ((e = set_smem(k_ring_idft<T, IN_FOLD>, b)) != cudaSuccess) return e;
     return set_smem(k_ring_idft<T, IN_BINS>, b);
 }
-cudaError_t set_ring_kernel_limits(int Mmax) { return set_ring_kernel_limits_t<double>(Mmax); }
-
-template <typename T>
-size_t smem_bytes(int k0, int cnt, int M) {
-    if (M == 0) { int N = 2 * (k0 + cnt - 1) + 1; return sizeof(cplx_t<T>) * 3 * (size_t)N; }
-    return sizeof(cplx_t<T>) * (size_t)M;
-}
 
 }  // namespace
 
 cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s) {
-    int Mmax = 2;
-    for (int j = 5; (1 << j) < L; ++j) Mmax = 1 << (j + 3);
-    dp.Mmax = Mmax;
-    dp.h_filt_off.assign(L, -1);
-    dp.h_filt_M.assign(L, 0);
+    // ring classes: the direct rings, then runs of consecutive k sharing the chirp-z length
+    dp.classes.clear();
+    const int kd = std::min(L, (kDirectMaxN + 1) / 2);
+    dp.classes.push_back(RingClass{0, kd, 0, 0});
+    int Mmax = 0;
     int64_t total = 0;
-    for (int k = 32; k < L; ++k) {
-        int N = 2 * k + 1, M = 1 << ilog2(2 * N - 1);
-        dp.h_filt_off[k] = total;
-        dp.h_filt_M[k] = M;
+    for (int k = kd; k < L; ++k) {
+        const int M = bluestein_length(2 * k + 1);
+        if (dp.classes.back().M != M) dp.classes.push_back(RingClass{k, 0, M, total});
+        dp.classes.back().cnt += 1;
         total += M;
+        Mmax = std::max(Mmax, M);
     }
+    dp.Mmax = Mmax;
+    // twiddle table length: a multiple of every 2^a and 3 * 2^a length used
+    int p2 = 16;
+    while (p2 < Mmax) p2 <<= 1;
+    dp.Mtab = 3 * p2;
+    dp.filt_total = total;
     cudaError_t e;
-    size_t b_tw = sizeof(double2) * Mmax, b_ch = sizeof(double2) * (size_t)L * L;
-    size_t b_f = sizeof(double2) * (size_t)(total > 0 ? total : 1);
+    const size_t b_tw = sizeof(double2) * dp.Mtab, b_ch = sizeof(double2) * (size_t)L * L;
+    const size_t b_f = sizeof(double2) * (size_t)(total > 0 ? total : 1);
     if ((e = cudaMalloc(&dp.twiddle, b_tw)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&dp.chirp, b_ch)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&dp.filt, b_f)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&dp.filt_off, sizeof(int64_t) * L)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&dp.filt_M, sizeof(int) * L)) != cudaSuccess) return e;
-    bytes = b_tw + b_ch + b_f + sizeof(int64_t) * L + sizeof(int) * L;
-    dp.filt_total = total;
-    cudaMemcpyAsync(dp.filt_off, dp.h_filt_off.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice, s);
-    cudaMemcpyAsync(dp.filt_M, dp.h_filt_M.data(), sizeof(int) * L, cudaMemcpyHostToDevice, s);
-    k_twiddle<<<(Mmax + 255) / 256, 256, 0, s>>>(dp.twiddle, Mmax);
-    int64_t LL = (int64_t)L * L;
+    bytes = b_tw + b_ch + b_f;
+    k_twiddle<<<(dp.Mtab + 255) / 256, 256, 0, s>>>(dp.twiddle, dp.Mtab);
+    const int64_t LL = (int64_t)L * L;
     k_chirp<<<(unsigned)((LL + 255) / 256), 256, 0, s>>>(dp.chirp, L);
-    if ((e = set_ring_kernel_limits(Mmax)) != cudaSuccess) return e;
-    if (L > 32) {
-        if ((e = set_smem(k_filter, sizeof(double2) * Mmax)) != cudaSuccess) return e;
-        e = for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
-            if (M == 0 || cnt <= 0) return cudaSuccess;
-            k_filter<<<cnt, 256, sizeof(double2) * M, s>>>(k0, dp.chirp, dp.filt_off, dp.filt_M,
-                                                          dp.twiddle, Mmax, dp.filt);
-            return cudaGetLastError();
-        });
-        if (e != cudaSuccess) return e;
+    if ((e = set_ring_kernel_limits_t<double>(Mmax)) != cudaSuccess) return e;
+    if ((e = set_smem(k_filter, sizeof(double2) * (size_t)std::max(Mmax, 16))) != cudaSuccess) return e;
+    for (const RingClass &rc : dp.classes) {
+        if (rc.M == 0 || rc.cnt <= 0) continue;
+        k_filter<<<rc.cnt, kThreads, sizeof(double2) * rc.M, s>>>(rc.k0, rc.M, stages_of(rc.M), dp.chirp,
+                                                                  dp.twiddle, dp.Mtab, dp.filt + rc.filt_off);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
 
 cudaError_t dft_plan_make_f32(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s) {
-    const int64_t n_tw = dp.Mmax, n_ch = (int64_t)L * L, n_f = dp.filt_total > 0 ? dp.filt_total : 1;
+    const int64_t n_tw = dp.Mtab, n_ch = (int64_t)L * L, n_f = dp.filt_total > 0 ? dp.filt_total : 1;
     cudaError_t e;
     if ((e = cudaMalloc(&dp.twiddle_f, sizeof(float2) * n_tw)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&dp.chirp_f, sizeof(float2) * n_ch)) != cudaSuccess) return e;
@@ -406,32 +608,37 @@ cudaError_t dft_plan_make_f32(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t 
 void dft_plan_destroy(DftPlan &dp) {
     cudaFree(dp.twiddle_f); cudaFree(dp.chirp_f); cudaFree(dp.filt_f);
     cudaFree(dp.twiddle); cudaFree(dp.chirp); cudaFree(dp.filt);
-    cudaFree(dp.filt_off); cudaFree(dp.filt_M);
     dp = DftPlan{};
 }
+
+int64_t dft_launches(const DftPlan &dp) { return (int64_t)dp.classes.size(); }
 
 template <typename T, int OUT>
 static cudaError_t ring_dft_impl(int L, const DftPlan &dp, const cplx_t<T> *samples, T *out,
                                  int64_t batch, cudaStream_t s) {
-    return for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
-        if (cnt <= 0) return cudaSuccess;
-        size_t sm = smem_bytes<T>(k0, cnt, M);
-        dim3 grid(cnt, (unsigned)batch);
-        k_ring_dft<T, OUT><<<grid, M == 0 ? 64 : 256, sm, s>>>(make_args<T>(L, dp, batch, k0, M), samples, out);
-        return cudaGetLastError();
-    });
+    for (const RingClass &rc : dp.classes) {
+        if (rc.cnt <= 0) continue;
+        const dim3 grid(rc.cnt, (unsigned)batch);
+        k_ring_dft<T, OUT><<<grid, rc.M == 0 ? 64 : kThreads, smem_bytes<T>(rc), s>>>(
+            make_args<T>(L, dp, batch, rc), samples, out);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 template <typename T, int IN>
 static cudaError_t ring_idft_impl(int L, const DftPlan &dp, const T *in, cplx_t<T> *samples,
                                   int64_t batch, cudaStream_t s) {
-    return for_each_class(L, [&](int k0, int cnt, int M) -> cudaError_t {
-        if (cnt <= 0) return cudaSuccess;
-        size_t sm = smem_bytes<T>(k0, cnt, M);
-        dim3 grid(cnt, (unsigned)batch);
-        k_ring_idft<T, IN><<<grid, M == 0 ? 64 : 256, sm, s>>>(make_args<T>(L, dp, batch, k0, M), in, samples);
-        return cudaGetLastError();
-    });
+    for (const RingClass &rc : dp.classes) {
+        if (rc.cnt <= 0) continue;
+        const dim3 grid(rc.cnt, (unsigned)batch);
+        k_ring_idft<T, IN><<<grid, rc.M == 0 ? 64 : kThreads, smem_bytes<T>(rc), s>>>(
+            make_args<T>(L, dp, batch, rc), in, samples);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t ring_dft_to_bins(int L, const DftPlan &dp, const double2 *samples, double *W,

@@ -71,18 +71,24 @@ constexpr int kSplitCap = 16;
 // Rings whose DFT is taken directly (O(N^2)); longer rings use Bluestein's chirp-z transform.
 constexpr int kDirectMaxN = 63;
 
+// Consecutive rings k0 .. k0 + cnt - 1 sharing one chirp-z convolution length M (M = 0: rings
+// short enough for the direct DFT); their filters start at filt_off, M values per ring.
+struct RingClass {
+    int k0, cnt, M;
+    int64_t filt_off;
+};
+
 struct DftPlan {
-    int Mmax = 0;                  // largest power-of-two convolution length
+    int Mmax = 0;                  // largest convolution length (2^a or 3 * 2^a)
+    int Mtab = 0;                  // twiddle table length: a multiple of every convolution length
     double2 *chirp = nullptr;      // e^{-i pi n^2 / N_k}, n < N_k, ring k at offset k^2
-    double2 *filt = nullptr;       // per Bluestein ring: FFT_M of the conjugate chirp, scaled
-    int64_t *filt_off = nullptr;   // device, per ring (-1 for direct rings)
-    int *filt_M = nullptr;         // device, per ring convolution length (0 for direct rings)
-    double2 *twiddle = nullptr;    // e^{-2 pi i t / Mmax}, t < Mmax
+    double2 *filt = nullptr;       // per chirp-z ring: FFT_M of the conjugate chirp, scaled 1/M,
+                                   // in the forward FFT's digit-reversed output order
+    double2 *twiddle = nullptr;    // e^{-2 pi i t / Mtab}, t < Mtab
     int64_t filt_total = 0;        // complex values in filt
     // SHT_F32 plans: the same tables rounded to float32 (dft_plan_make_f32)
     float2 *chirp_f = nullptr, *filt_f = nullptr, *twiddle_f = nullptr;
-    std::vector<int64_t> h_filt_off;
-    std::vector<int> h_filt_M;
+    std::vector<RingClass> classes;
 };
 
 // Per-call device scratch, sized for `batch` signals.
@@ -193,6 +199,8 @@ cudaError_t spin_inverse_adjoint(sht_plan_t p, const double2 *d_samples, double2
 // dft.cu
 cudaError_t dft_plan_create(int L, DftPlan &dp, uint64_t &bytes, cudaStream_t s);
 void dft_plan_destroy(DftPlan &dp);
+// kernel launches of one ring-DFT pass (one per ring class)
+int64_t dft_launches(const DftPlan &dp);
 // forward ring DFTs of every ring of every signal, 1/N scaled, into the order-major bins W
 cudaError_t ring_dft_to_bins(int L, const DftPlan &dp, const double2 *samples, double *W,
                              int64_t batch, bool scale, cudaStream_t s);
