@@ -636,6 +636,91 @@ def _time_form(dtype, L, B, theta, c, steps, warmup, refine_iters, peaks, sm_mhz
     return out
 
 
+def run_uneven(args):
+    """The uneven-batch workload on a bounded draw: nsig signals with L log-uniform in [lo, hi]
+    (seeded), f_lm re/im uniform[-1, 1]; one plan per distinct L (greedy rings, plan time
+    reported apart); inverse then forward of the whole batch as one persistent launch per
+    direction (sht_uneven_*), captured in a CUDA graph, beside the per-plan grouped calls."""
+    import torch
+
+    from paper_1403_4661_gb300 import build, synth
+    from paper_1403_4661_gb300.sht import Plan, UnevenBatch, forward_uneven, inverse_uneven
+
+    build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    Ls = [int(L) for L in synth.loguniform_bandlimits(args.uneven_n, args.uneven_lo, args.uneven_hi, 4)]
+    distinct = sorted(set(Ls))
+    t0 = time.time()
+    plans = [Plan(L, dtype=args.dtype) for L in distinct]
+    plan_s = time.time() - t0
+    index = [distinct.index(L) for L in Ls]
+    offsets, pos = [], 0
+    for L in Ls:
+        offsets.append(pos)
+        pos += L * L
+    packed = np.concatenate([synth.uniform_coeffs(L, 1, 5000 + i)[0] for i, L in enumerate(Ls)])
+    c = torch.from_numpy(packed).to(dev)
+    s, c2 = torch.zeros_like(c), torch.zeros_like(c)
+    ub = UnevenBatch(plans, index, offsets)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ub.inverse(c, out=s)
+        ub.forward(s, out=c2)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ub.check()
+    err = float((c2 - c).abs().max())
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g):
+            step()
+    stream.wait_stream(side)
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the same batch through the grouped per-plan calls (eager)
+    for _ in range(2):
+        forward_uneven(plans, index, offsets, inverse_uneven(plans, index, offsets, c))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(max(1, args.steps // 2)):
+        forward_uneven(plans, index, offsets, inverse_uneven(plans, index, offsets, c))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_grouped = e0.elapsed_time(e1) / max(1, args.steps // 2)
+    flops = sum(8.0 * L ** 3 for L in Ls)   # inverse 4 L^3 + forward 4 L^3 per signal (Sec. IV-C counts)
+    line = {
+        "metric": "uneven batch fwd+inv signals/s (one persistent launch per direction)",
+        "value": len(Ls) / (ms * 1e-3), "unit": "signals/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{len(Ls)} complex signals, L log-uniform in [{args.uneven_lo}, {args.uneven_hi}] "
+                               f"(seed 4), f_lm re/im iid U[-1,1]; inverse then forward",
+                   "distinct_L": len(distinct), "L_max": max(Ls), "plan_arithmetic": args.dtype,
+                   "launch": "one CUDA graph per step: two cooperative launches"},
+        "grouped_calls": {"ms_per_step": ms_grouped, "value": len(Ls) / (ms_grouped * 1e-3)},
+        "roofline": {"bound": "alu", "kernel": "k_uneven_inverse + k_uneven_forward (float64 SIMT)",
+                     "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                     "frac": flops / (ms * 1e-3) / 1e12 / FP64_TFLOPS_NOMINAL,
+                     "flops_per_step": flops, "flops_definition": "sum over signals of 8 L^3"},
+        "accuracy": {"E1_max_round_trip": err},
+        "plan_seconds": plan_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -655,7 +740,15 @@ def main():
     ap.add_argument("--forms-refine-iters", type=int, default=5,
                     help="fixed iteration count of the tf32_refined form (5 reaches the float64 "
                          "path's round-trip error at L=1024)")
+    ap.add_argument("--uneven", action="store_true",
+                    help="time the uneven-batch workload (one persistent launch per direction) instead")
+    ap.add_argument("--uneven-n", type=int, default=512)
+    ap.add_argument("--uneven-lo", type=int, default=32)
+    ap.add_argument("--uneven-hi", type=int, default=256)
     args = ap.parse_args()
+    if args.uneven:
+        run_uneven(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

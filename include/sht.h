@@ -227,6 +227,42 @@ sht_status sht_inverse_uneven(const sht_plan_t *plans, int nplans, int64_t nsig,
                               const int64_t *offsets, const void *d_coeffs, void *d_samples, void *stream);
 
 /*
+ * Uneven batches in one persistent launch per direction (a project addition: the per-signal
+ * transforms are the paper's Procedures 1 and 2, batching signals of different band-limits is not
+ * in the paper).
+ *   sht_uneven_create - describe a batch once: nsig signals, signal i transformed by
+ *     plans[plan_index[i]] (complex128 scalar plans of any arithmetic, created beforehand on the
+ *     current device and kept alive while the batch object exists) and occupying the L^2 complex128
+ *     values (L of its plan) at complex-element offset offsets[i] of the input and output arrays
+ *     (samples ring-major, coefficients at l^2 + l + m).  Host arrays, read during the call only.
+ *     Copies the descriptors to the device and allocates the scratch of every signal (about
+ *     32 L^2 bytes each).  SHT_ERR_INVALID_ARG for an index outside [0, nplans), a negative offset or
+ *     overlapping signals; SHT_ERR_UNSUPPORTED for SHT_F32 or spin plans.  Blocking.
+ *   sht_uneven_forward / sht_uneven_inverse - the whole batch in ONE cooperative launch whose CTAs
+ *     stay resident and walk its work items: inverse = synthesis per (signal, order), one grid
+ *     barrier, fold + inverse ring DFT per (signal, ring); forward = ring DFT per (signal, ring),
+ *     one grid barrier, then each signal's order chain (solves and alias subtractions, m = L-1..0)
+ *     on one CTA, largest L first.  float64 SIMT arithmetic on the plans' float64 tables (results
+ *     float64-accurate, as the batched calls).  Device buffers 16-byte aligned, input and output
+ *     disjoint.  Stream-ordered; allocates nothing and never synchronises (capturable in a CUDA
+ *     graph); calls on one batch object must not overlap in time (they share its scratch).
+ *   sht_uneven_set_wait_limit - limit (1e-9 .. 60 s; default: that of plans[0]) of the grid
+ *     barrier's wait; a CTA that reaches it abandons the call (results invalid) and sets the
+ *     batch's status word.
+ *   sht_uneven_check - synchronise the device and report SHT_ERR_TIMEOUT if a barrier gave up
+ *     since the last check (clears the flag).
+ *   sht_uneven_destroy - free the batch object (synchronises the device; the plans are not freed).
+ */
+typedef struct sht_uneven_s *sht_uneven_t;
+sht_status sht_uneven_create(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                             const int64_t *offsets, sht_uneven_t *out);
+sht_status sht_uneven_forward(sht_uneven_t batch, const void *d_samples, void *d_coeffs, void *stream);
+sht_status sht_uneven_inverse(sht_uneven_t batch, const void *d_coeffs, void *d_samples, void *stream);
+sht_status sht_uneven_set_wait_limit(sht_uneven_t batch, double seconds);
+sht_status sht_uneven_check(sht_uneven_t batch);
+sht_status sht_uneven_destroy(sht_uneven_t batch);
+
+/*
  * sht_inverse_adjoint - the adjoint A^H of the inverse map A (A[(k,n),(l,m)] = Y_l^m(theta_k,
  *   phi_kn)): coefficients-shaped output from samples-shaped input,
  *   out_l^m = sum_{k,n} P~_l^m(theta_k) e^{-i m phi_kn} y_kn.  Same layouts as sht_forward.

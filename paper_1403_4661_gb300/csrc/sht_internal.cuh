@@ -89,6 +89,8 @@ struct DftPlan {
     // SHT_F32 plans: the same tables rounded to float32 (dft_plan_make_f32)
     float2 *chirp_f = nullptr, *filt_f = nullptr, *twiddle_f = nullptr;
     std::vector<RingClass> classes;
+    int *d_ring_M = nullptr;           // device, per ring: chirp-z length (0: direct ring)
+    int64_t *d_ring_foff = nullptr;    // device, per ring: offset of its filter in filt
 };
 
 // Per-call device scratch, sized for `batch` signals.

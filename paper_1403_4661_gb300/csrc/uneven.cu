@@ -1,0 +1,529 @@
+// Uneven batches (signals of different band-limits L_i) in ONE persistent launch per direction.
+//
+// The per-signal transform is the paper's (Procedure 1 in bin space, Eqs. (14)-(16); Procedure 2,
+// Eqs. (11), (18)); batching signals of uneven L is this library's.  The batch is described once
+// (sht_uneven_create: every signal's plan and offset, copied to the device), then each call is one
+// cooperative launch of a grid that stays resident and walks the batch's work items:
+//
+//   inverse  phase 1: items (signal i, order m), L_i per signal: G_{+-m}(theta_k) for every ring k
+//                     of signal i (Eq. (11)), from its coefficients and its plan's P~ block m;
+//            grid barrier;
+//            phase 2: items (signal i, ring k): fold of the orders into the ring's 2k+1 bins and
+//                     the inverse ring DFT (Eq. (18)), with the plan's chirp-z tables;
+//   forward  phase 1: items (signal i, ring k): ring DFT into the signal's order-major bins;
+//            grid barrier;
+//            phase 2: items = signals, largest L first: one CTA runs a signal's whole order chain,
+//                     m = L-1..0, solve (plan's P_m^{-1}) and alias subtraction (plan's P~ block m),
+//                     with block-level synchronisation only.
+//
+// All arithmetic is float64 on the SIMT pipes, on the plans' float64 tables (every complex128
+// scalar plan keeps them).  Items of one phase are independent; the only grid-wide wait is the
+// barrier between the phases, which is bounded (the plan wait limit of the first plan): a CTA that
+// gives up sets the batch's status word and an abort word, and every CTA leaves.  The cooperative
+// launch guarantees that all CTAs are resident, so the barrier cannot wait on a CTA that never
+// runs.  Scratch (bins or synthesis table per signal) is allocated by sht_uneven_create; a call
+// allocates nothing and synchronises nothing.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "fft_device.cuh"
+
+namespace sht {
+namespace {
+
+using namespace fft;
+
+constexpr int kUThreads = 256;
+
+struct UPlan {
+    int L, Mtab;
+    const double *pt, *pinv;                    // P~ table, per-order inverses (scalar layouts)
+    const double2 *chirp, *filt, *tw;           // ring DFT tables
+    const int *ring_M;                          // per ring: chirp-z length (0: direct)
+    const int64_t *ring_foff;                   // per ring: filter offset
+};
+
+struct USig {
+    int plan, L;
+    int64_t off;      // complex-element offset of the signal in the caller's arrays
+    int64_t ws;       // double offset of the signal's scratch (4 columns per row)
+    int64_t item0;    // first item of the signal in the per-(signal, order / ring) phases
+};
+
+struct UArgs {
+    const UPlan *plans;
+    const USig *sigs;
+    const int *lpt;   // signal indices by descending L
+    int nsig;
+    int64_t items;    // sum of L_i
+    double *ws;
+    unsigned *bar;    // [0] arrivals, [32] abort (separate 128-byte lines)
+    int *status;
+    uint64_t wait_ns;
+    const double2 *in;
+    double2 *out;
+};
+
+__device__ __forceinline__ uint64_t now_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Signal of work item `it` (sigs ordered by item0).
+__device__ __forceinline__ int item_signal(const UArgs &a, int64_t it) {
+    int lo = 0, hi = a.nsig - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.sigs[mid].item0 <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One grid-wide barrier (the only one of a launch); false once any CTA has given up.
+__device__ bool grid_barrier_once(const UArgs &a, int *flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(a.bar, 1u);
+        volatile unsigned *cnt = a.bar, *abort_w = a.bar + 32;
+        const uint64_t t0 = now_ns();
+        while (*cnt < gridDim.x) {
+            if (*abort_w) { ok = 0; break; }
+            if (now_ns() - t0 > a.wait_ns) {
+                atomicOr(a.status, 2);
+                atomicExch(a.bar + 32, 1u);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// ---- inverse ----------------------------------------------------------------------------------
+
+// Bin t of ring k (2k+1 bins) folded from the signal's synthesis table G (rows (|m|, k), 4
+// columns): sum over m = q mod N, |m| < L; threads of `group` (g = 0..G-1) split the orders.
+__device__ __forceinline__ double2 fold_part(const double *__restrict__ G, int L, int k, int t, int g, int Gn) {
+    const int N = 2 * k + 1, q = t <= k ? t : t - N;
+    double ax = 0.0, ay = 0.0;
+    for (int m = q - ((q + L - 1) / N) * N + g * N; m <= L - 1; m += Gn * N) {
+        const int o = m < 0 ? -m : m;
+        const double *p = G + ((int64_t)o * L + k) * 4 + (m < 0 ? 2 : 0);
+        ax += __ldcg(p);       // written by other CTAs before the grid barrier: read through L2
+        ay += __ldcg(p + 1);
+    }
+    return make_double2(ax, ay);
+}
+
+__global__ void __launch_bounds__(kUThreads) k_uneven_inverse(UArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *xs = reinterpret_cast<double *>(smem_raw);
+    double2 *sm = reinterpret_cast<double2 *>(smem_raw);
+    __shared__ int s_flag;
+    const int tid = threadIdx.x;
+    // phase 1: G_{+-m}(theta_k) = sum_l P~_l^m(theta_k) (f_l^m, (-1)^m f_l^{-m}) for all k
+    for (int64_t it = blockIdx.x; it < a.items; it += gridDim.x) {
+        const USig sg = a.sigs[item_signal(a, it)];
+        const UPlan pl = a.plans[sg.plan];
+        const int L = sg.L, m = (int)(it - sg.item0), n = L - m;
+        const double2 *c = a.in + sg.off;
+        __syncthreads();   // the previous item is done with xs
+        for (int r = tid; r < n; r += blockDim.x) {
+            const int l = m + r;
+            const double2 p = c[(int64_t)l * l + l + m];
+            double2 q = make_double2(0.0, 0.0);
+            if (m > 0) {
+                q = c[(int64_t)l * l + l - m];
+                if (m & 1) { q.x = -q.x; q.y = -q.y; }
+            }
+            xs[4 * r] = p.x; xs[4 * r + 1] = p.y; xs[4 * r + 2] = q.x; xs[4 * r + 3] = q.y;
+        }
+        __syncthreads();
+        const double *P = pl.pt + pt_off(L, m);
+        double *G = a.ws + sg.ws + (int64_t)m * L * 4;
+        for (int k = tid; k < L; k += blockDim.x) {
+            const double *row = P + (int64_t)k * n;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            for (int r = 0; r < n; ++r) {
+                const double pv = __ldg(row + r);
+                s0 = fma(pv, xs[4 * r], s0);
+                s1 = fma(pv, xs[4 * r + 1], s1);
+                s2 = fma(pv, xs[4 * r + 2], s2);
+                s3 = fma(pv, xs[4 * r + 3], s3);
+            }
+            double *g = G + 4 * (int64_t)k;
+            g[0] = s0; g[1] = s1; g[2] = s2; g[3] = s3;
+        }
+    }
+    if (!grid_barrier_once(a, &s_flag)) return;
+    // phase 2: fold + inverse ring DFT per (signal, ring)
+    for (int64_t it = blockIdx.x; it < a.items; it += gridDim.x) {
+        const USig sg = a.sigs[item_signal(a, it)];
+        const UPlan pl = a.plans[sg.plan];
+        const int L = sg.L, k = (int)(it - sg.item0), N = 2 * k + 1;
+        const double *G = a.ws + sg.ws;
+        double2 *y = a.out + sg.off + (int64_t)k * k;
+        const int M = __ldg(pl.ring_M + k);
+        __syncthreads();   // the previous item is done with the shared buffer
+        if (M == 0) {
+            // direct ring: bins by groups of threads, then the direct sum with a root table
+            double2 *B = sm, *roots = sm + N, *part = sm + 2 * N;
+            const int Gn = max(1, (int)blockDim.x / N);
+            for (int t = tid; t < N * Gn; t += blockDim.x) part[t] = fold_part(G, L, k, t % N, t / N, Gn);
+            for (int t = tid; t < N; t += blockDim.x) {
+                double s, cc;
+                sincospi(2.0 * (double)t / (double)N, &s, &cc);
+                roots[t] = make_double2(cc, s);   // e^{+2 pi i t / N}
+            }
+            __syncthreads();
+            for (int j = tid; j < N; j += blockDim.x) {
+                double2 acc = part[j];
+                for (int g = 1; g < Gn; ++g) acc = cadd(acc, part[g * N + j]);
+                B[j] = acc;
+            }
+            __syncthreads();
+            for (int nn = tid; nn < N; nn += blockDim.x) {
+                double2 acc = make_double2(0.0, 0.0);
+                int idx = 0;
+                for (int j = 0; j < N; ++j) {
+                    acc = cadd(acc, cmul(B[j], roots[idx]));
+                    idx += nn; if (idx >= N) idx -= N;
+                }
+                y[nn] = acc;
+            }
+            continue;
+        }
+        const Stages st = stages_of(M);
+        const double2 *cz = pl.chirp + (int64_t)k * k;
+        const double2 *f = pl.filt + __ldg(pl.ring_foff + k);
+        bluestein(sm, N, M, st, pl.tw, pl.Mtab, cz, f,
+                  [&](int t) { return conjd(fold_part(G, L, k, t, 0, 1)); },
+                  [&](int t, double2 v) { y[t] = conjd(v); });
+    }
+}
+
+// ---- forward ----------------------------------------------------------------------------------
+
+// Bin t of ring k into the signal's order-major bins W (rows rows_off(L, |q|) + k - |q|, 4
+// columns), scaled 1/N.
+__device__ __forceinline__ void store_bin_u(double *W, int L, int k, int t, double2 v) {
+    const int N = 2 * k + 1, q = t <= k ? t : t - N;
+    const double sc = 1.0 / (double)N;
+    const int o = q < 0 ? -q : q;
+    double *w = W + (rows_off(L, o) + (k - o)) * 4;
+    if (q >= 0) { w[0] = v.x * sc; w[1] = v.y * sc; }
+    else        { w[2] = v.x * sc; w[3] = v.y * sc; }
+    if (q == 0) { w[2] = 0.0; w[3] = 0.0; }
+}
+
+__global__ void __launch_bounds__(kUThreads) k_uneven_forward(UArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double2 *sm = reinterpret_cast<double2 *>(smem_raw);
+    double *ds = reinterpret_cast<double *>(smem_raw);
+    __shared__ int s_flag;
+    const int tid = threadIdx.x;
+    // phase 1: ring DFTs into bins
+    for (int64_t it = blockIdx.x; it < a.items; it += gridDim.x) {
+        const USig sg = a.sigs[item_signal(a, it)];
+        const UPlan pl = a.plans[sg.plan];
+        const int L = sg.L, k = (int)(it - sg.item0), N = 2 * k + 1;
+        double *W = a.ws + sg.ws;
+        const double2 *x = a.in + sg.off + (int64_t)k * k;
+        const int M = __ldg(pl.ring_M + k);
+        __syncthreads();
+        if (M == 0) {
+            double2 *xs = sm, *roots = sm + N;
+            for (int t = tid; t < N; t += blockDim.x) {
+                xs[t] = x[t];
+                double s, cc;
+                sincospi(2.0 * (double)t / (double)N, &s, &cc);
+                roots[t] = make_double2(cc, -s);   // e^{-2 pi i t / N}
+            }
+            __syncthreads();
+            for (int j = tid; j < N; j += blockDim.x) {
+                double2 acc = make_double2(0.0, 0.0);
+                int idx = 0;
+                for (int nn = 0; nn < N; ++nn) {
+                    acc = cadd(acc, cmul(xs[nn], roots[idx]));
+                    idx += j; if (idx >= N) idx -= N;
+                }
+                store_bin_u(W, L, k, j, acc);
+            }
+            continue;
+        }
+        const Stages st = stages_of(M);
+        const double2 *cz = pl.chirp + (int64_t)k * k;
+        const double2 *f = pl.filt + __ldg(pl.ring_foff + k);
+        bluestein(sm, N, M, st, pl.tw, pl.Mtab, cz, f,
+                  [&](int t) { return x[t]; },
+                  [&](int t, double2 v) { store_bin_u(W, L, k, t, v); });
+    }
+    if (!grid_barrier_once(a, &s_flag)) return;
+    // phase 2: one signal's order chain per CTA, largest L first
+    for (int idx = blockIdx.x; idx < a.nsig; idx += gridDim.x) {
+        const USig sg = a.sigs[a.lpt[idx]];
+        const UPlan pl = a.plans[sg.plan];
+        const int L = sg.L;
+        double *W = a.ws + sg.ws;
+        double2 *co = a.out + sg.off;
+        double *g = ds, *fm = ds + 4 * L;
+        for (int m = L - 1; m >= 0; --m) {
+            const int n = L - m;
+            __syncthreads();   // W holds the previous order's alias subtraction
+            // g_m: bins +-m of rings k >= m (Eq. (11)), free of the orders above m by now
+            const double *Wm = W + rows_off(L, m) * 4;
+            for (int i = tid; i < 4 * n; i += blockDim.x) g[i] = __ldcg(Wm + i);   // other CTAs wrote the bins
+            __syncthreads();
+            // Eq. (14): F_m = P_m^{-1} g_m; f_l^{+m} and f_l^{-m} = (-1)^m F^{-}
+            const double *Pi = pl.pinv + pinv_off(L, m);
+            for (int r = tid; r < n; r += blockDim.x) {
+                const double *row = Pi + (int64_t)r * n;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int cc = 0; cc < n; ++cc) {
+                    const double pv = __ldg(row + cc);
+                    s0 = fma(pv, g[4 * cc], s0);
+                    s1 = fma(pv, g[4 * cc + 1], s1);
+                    s2 = fma(pv, g[4 * cc + 2], s2);
+                    s3 = fma(pv, g[4 * cc + 3], s3);
+                }
+                fm[4 * r] = s0; fm[4 * r + 1] = s1; fm[4 * r + 2] = s2; fm[4 * r + 3] = s3;
+                const int l = m + r;
+                double2 *cl = co + (int64_t)l * l + l;
+                cl[m] = make_double2(s0, s1);
+                if (m > 0) cl[-m] = (m & 1) ? make_double2(-s2, -s3) : make_double2(s2, s3);
+            }
+            if (m == 0) break;
+            __syncthreads();
+            // Eqs. (15)-(16): G_{+-m}(theta_k), k < m, out of bins alias_k(+-m) of ring k
+            const double *Pt = pl.pt + pt_off(L, m);
+            for (int k = tid; k < m; k += blockDim.x) {
+                const double *row = Pt + (int64_t)k * n;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int r = 0; r < n; ++r) {
+                    const double pv = __ldg(row + r);
+                    s0 = fma(pv, fm[4 * r], s0);
+                    s1 = fma(pv, fm[4 * r + 1], s1);
+                    s2 = fma(pv, fm[4 * r + 2], s2);
+                    s3 = fma(pv, fm[4 * r + 3], s3);
+                }
+                const int aa = alias_bin(m, k), o = aa < 0 ? -aa : aa;
+                double *w = W + (rows_off(L, o) + (k - o)) * 4;
+                if (aa == 0) {
+                    w[0] = __ldcg(w) - (s0 + s2);
+                    w[1] = __ldcg(w + 1) - (s1 + s3);
+                } else {
+                    const int sp = aa > 0 ? 0 : 2, sq = 2 - sp;   // slots of bins aa and -aa
+                    w[sp] = __ldcg(w + sp) - s0; w[sp + 1] = __ldcg(w + sp + 1) - s1;
+                    w[sq] = __ldcg(w + sq) - s2; w[sq + 1] = __ldcg(w + sq + 1) - s3;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+}  // namespace sht
+
+using namespace sht;
+
+struct sht_uneven_s {
+    int device = 0;
+    int nsig = 0;
+    int64_t items = 0;
+    int64_t span = 0;              // complex elements covered: max(offset + L^2)
+    std::vector<sht_plan_t> plans;
+    UPlan *d_plans = nullptr;
+    USig *d_sigs = nullptr;
+    int *d_lpt = nullptr;
+    double *ws = nullptr;
+    unsigned *bar = nullptr;       // 64 words: arrival counter and abort word
+    int *status = nullptr;
+    size_t smem = 0;
+    int grid_inv = 0, grid_fwd = 0;
+    uint64_t wait_ns = 1000000000ull;
+    uint64_t bytes = 0;
+};
+
+namespace {
+
+void uneven_free(sht_uneven_t u) {
+    if (!u) return;
+    cudaFree(u->d_plans); cudaFree(u->d_sigs); cudaFree(u->d_lpt); cudaFree(u->ws);
+    cudaFree(u->bar); cudaFree(u->status);
+    delete u;
+}
+
+template <typename K>
+cudaError_t coop_grid(K kernel, size_t smem, int *grid) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kUThreads, smem)) != cudaSuccess) return e;
+    *grid = sms * per_sm;
+    return *grid > 0 ? cudaSuccess : cudaErrorInvalidConfiguration;
+}
+
+sht_status uneven_launch(sht_uneven_t u, bool forward, const void *d_in, void *d_out, void *stream) {
+    if (!u) return set_error(SHT_ERR_INVALID_ARG, "uneven batch is NULL");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
+    if (dev != u->device) return set_error(SHT_ERR_INVALID_ARG, "current device is not the batch's device");
+    if (u->nsig == 0) return SHT_OK;
+    if (!d_in || !d_out) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");
+    if (((uintptr_t)d_in & 15u) || ((uintptr_t)d_out & 15u))
+        return set_error(SHT_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    const uintptr_t bytes = (uintptr_t)16 * (uintptr_t)u->span, a = (uintptr_t)d_in, b = (uintptr_t)d_out;
+    if (a < b + bytes && b < a + bytes) return set_error(SHT_ERR_INVALID_ARG, "input and output overlap");
+    cudaStream_t s = (cudaStream_t)stream;
+    UArgs args{u->d_plans, u->d_sigs, u->d_lpt, u->nsig, u->items, u->ws, u->bar, u->status, u->wait_ns,
+               (const double2 *)d_in, (double2 *)d_out};
+    if ((e = cudaMemsetAsync(u->bar, 0, 64 * sizeof(unsigned), s)) != cudaSuccess) return cuda_check(e, "uneven barrier");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(forward ? u->grid_fwd : u->grid_inv));
+    cfg.blockDim = dim3(kUThreads);
+    cfg.dynamicSmemBytes = u->smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = forward ? cudaLaunchKernelEx(&cfg, k_uneven_forward, args) : cudaLaunchKernelEx(&cfg, k_uneven_inverse, args);
+    return cuda_check(e, forward ? "sht_uneven_forward" : "sht_uneven_inverse");
+}
+
+}  // namespace
+
+extern "C" {
+
+sht_status sht_uneven_create(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,
+                             const int64_t *offsets, sht_uneven_t *out) {
+    if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nsig < 0 || nplans < 0) return set_error(SHT_ERR_INVALID_ARG, "negative count");
+    if (nsig > 0 && (!plans || !plan_index || !offsets || nplans == 0))
+        return set_error(SHT_ERR_INVALID_ARG, "NULL plan, index or offset array");
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
+    int Lmax = 1, Mmax = 16;
+    for (int g = 0; g < nplans; ++g) {
+        sht_status st = check_plan(plans[g]);
+        if (st != SHT_OK) return st;
+        if (plans[g]->dtype == SHT_F32)
+            return set_error(SHT_ERR_UNSUPPORTED, "uneven batches take complex128 plans (not SHT_F32)");
+        if (plans[g]->spin != 0) return set_error(SHT_ERR_UNSUPPORTED, "uneven batches take scalar (spin-0) plans");
+        Lmax = std::max(Lmax, plans[g]->L);
+        Mmax = std::max(Mmax, plans[g]->dft.Mmax);
+    }
+    // signals as intervals [offset, offset + L^2) of complex elements: in range, disjoint
+    std::vector<std::pair<int64_t, int64_t>> iv((size_t)nsig);
+    for (int64_t i = 0; i < nsig; ++i) {
+        const int g = plan_index[i];
+        if (g < 0 || g >= nplans) return set_error(SHT_ERR_INVALID_ARG, "plan index out of range");
+        if (offsets[i] < 0) return set_error(SHT_ERR_INVALID_ARG, "negative offset");
+        const int64_t L = plans[g]->L;
+        iv[(size_t)i] = {offsets[i], offsets[i] + L * L};
+    }
+    std::vector<std::pair<int64_t, int64_t>> sorted = iv;
+    std::sort(sorted.begin(), sorted.end());
+    for (size_t i = 1; i < sorted.size(); ++i)
+        if (sorted[i].first < sorted[i - 1].second) return set_error(SHT_ERR_INVALID_ARG, "signals overlap");
+
+    sht_uneven_t u = new sht_uneven_s;
+    u->device = dev;
+    u->nsig = (int)nsig;
+    u->plans.assign(plans, plans + nplans);
+    std::vector<UPlan> hp((size_t)nplans);
+    for (int g = 0; g < nplans; ++g) {
+        const sht_plan_t p = plans[g];
+        hp[(size_t)g] = UPlan{p->L, p->dft.Mtab, p->pt, p->pinv, p->dft.chirp, p->dft.filt, p->dft.twiddle,
+                              p->dft.d_ring_M, p->dft.d_ring_foff};
+    }
+    std::vector<USig> hs((size_t)nsig);
+    int64_t ws = 0, items = 0;
+    for (int64_t i = 0; i < nsig; ++i) {
+        const int g = plan_index[i], L = plans[g]->L;
+        hs[(size_t)i] = USig{g, L, offsets[i], ws, items};
+        ws += 4 * std::max<int64_t>(rows_total(L), (int64_t)L * L);   // bins (forward) or G (inverse)
+        items += L;
+        u->span = std::max(u->span, iv[(size_t)i].second);
+    }
+    u->items = items;
+    std::vector<int> lpt((size_t)nsig);
+    std::iota(lpt.begin(), lpt.end(), 0);
+    std::stable_sort(lpt.begin(), lpt.end(), [&](int x, int y) { return hs[(size_t)x].L > hs[(size_t)y].L; });
+    // shared memory: the largest chirp-z ring, the chain's two order vectors, the synthesis input
+    u->smem = std::max({sizeof(double2) * (size_t)Mmax, sizeof(double) * 8 * (size_t)Lmax,
+                        sizeof(double2) * (size_t)(2 * (2 * 31 + 1) + kUThreads + 2 * 63)});
+    u->wait_ns = nplans > 0 ? plans[0]->wait_ns : 1000000000ull;
+    const size_t b_ws = sizeof(double) * (size_t)std::max<int64_t>(ws, 1);
+    if ((e = cudaMalloc(&u->d_plans, sizeof(UPlan) * std::max<size_t>(hp.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&u->d_sigs, sizeof(USig) * std::max<size_t>(hs.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&u->d_lpt, sizeof(int) * std::max<size_t>(lpt.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&u->ws, b_ws)) != cudaSuccess ||
+        (e = cudaMalloc(&u->bar, 64 * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&u->status, sizeof(int))) != cudaSuccess) {
+        uneven_free(u);
+        return cuda_check(e, "uneven batch allocation");
+    }
+    u->bytes = b_ws + sizeof(UPlan) * hp.size() + sizeof(USig) * hs.size() + sizeof(int) * lpt.size();
+    if ((nplans && (e = cudaMemcpy(u->d_plans, hp.data(), sizeof(UPlan) * hp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (nsig && (e = cudaMemcpy(u->d_sigs, hs.data(), sizeof(USig) * hs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (nsig && (e = cudaMemcpy(u->d_lpt, lpt.data(), sizeof(int) * lpt.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemset(u->status, 0, sizeof(int))) != cudaSuccess ||
+        (e = coop_grid(k_uneven_inverse, u->smem, &u->grid_inv)) != cudaSuccess ||
+        (e = coop_grid(k_uneven_forward, u->smem, &u->grid_fwd)) != cudaSuccess) {
+        uneven_free(u);
+        return cuda_check(e, "uneven batch set-up");
+    }
+    *out = u;
+    return SHT_OK;
+}
+
+sht_status sht_uneven_forward(sht_uneven_t u, const void *d_samples, void *d_coeffs, void *stream) {
+    return uneven_launch(u, true, d_samples, d_coeffs, stream);
+}
+
+sht_status sht_uneven_inverse(sht_uneven_t u, const void *d_coeffs, void *d_samples, void *stream) {
+    return uneven_launch(u, false, d_coeffs, d_samples, stream);
+}
+
+sht_status sht_uneven_check(sht_uneven_t u) {
+    if (!u) return set_error(SHT_ERR_INVALID_ARG, "uneven batch is NULL");
+    int h = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&h, u->status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && h) e = cudaMemset(u->status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_check(e, "sht_uneven_check");
+    if (h) return set_error(SHT_ERR_TIMEOUT, "the grid barrier of an uneven-batch launch gave up");
+    return SHT_OK;
+}
+
+sht_status sht_uneven_set_wait_limit(sht_uneven_t u, double seconds) {
+    if (!u) return set_error(SHT_ERR_INVALID_ARG, "uneven batch is NULL");
+    if (!(seconds >= 1e-9 && seconds <= 60.0))
+        return set_error(SHT_ERR_INVALID_ARG, "wait limit must be in [1e-9, 60] seconds");
+    u->wait_ns = (uint64_t)(seconds * 1e9);
+    return SHT_OK;
+}
+
+sht_status sht_uneven_destroy(sht_uneven_t u) {
+    if (!u) return SHT_OK;
+    cudaDeviceSynchronize();
+    uneven_free(u);
+    return SHT_OK;
+}
+
+}  // extern "C"

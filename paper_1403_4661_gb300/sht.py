@@ -39,7 +39,8 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_forward_noalloc", "sht_plan_check", "sht_plan_set_refinement",
             "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit",
             "sht_plan_set_paths", "sht_plan_autotune", "sht_plan_save", "sht_plan_load",
-            "sht_plan_spin", "sht_plan_spin_with_thetas"]
+            "sht_plan_spin", "sht_plan_spin_with_thetas", "sht_uneven_create", "sht_uneven_forward",
+            "sht_uneven_inverse", "sht_uneven_set_wait_limit", "sht_uneven_check", "sht_uneven_destroy"]
 SHT_PATH_DEFAULT = 0
 SHT_PATH_TENSOR = 1
 SHT_PATH_SIMT = 2
@@ -104,6 +105,13 @@ def load_library(path=LIB_PATH):
         getattr(lib, name).argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(i64), P, P, P]
     lib.sht_plan_set_paths.argtypes = [P, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    lib.sht_uneven_create.argtypes = [ctypes.POINTER(P), ctypes.c_int, i64, ctypes.POINTER(ctypes.c_int),
+                                      ctypes.POINTER(i64), ctypes.POINTER(P)]
+    lib.sht_uneven_forward.argtypes = [P, P, P, P]
+    lib.sht_uneven_inverse.argtypes = [P, P, P, P]
+    lib.sht_uneven_set_wait_limit.argtypes = [P, ctypes.c_double]
+    lib.sht_uneven_check.argtypes = [P]
+    lib.sht_uneven_destroy.argtypes = [P]
     lib.sht_plan_save.argtypes = [P, ctypes.c_char_p]
     lib.sht_plan_load.argtypes = [ctypes.c_char_p, ctypes.c_int, ctypes.POINTER(P)]
     lib.sht_plan_autotune.argtypes = [P, i64, ctypes.POINTER(ShtTuning)]
@@ -269,6 +277,55 @@ def _uneven(name, plans, plan_index, offsets, x, out, stream):
     _check(getattr(load_library(), name)(hs, len(plans), n, idx, off, ctypes.c_void_p(x.data_ptr()),
                                          ctypes.c_void_p(y.data_ptr()), _stream_ptr(stream)))
     return y
+
+
+class UnevenBatch:
+    """A batch of signals of different band-limits transformed in one persistent launch per
+    direction (sht_uneven_create / sht_uneven_forward / sht_uneven_inverse).  The plans must stay
+    alive while the batch exists; signal i uses plans[plan_index[i]] at complex offset offsets[i]."""
+
+    def __init__(self, plans, plan_index, offsets):
+        lib = load_library()
+        self.plans = list(plans)
+        n = len(plan_index)
+        hs = (ctypes.c_void_p * max(1, len(self.plans)))(*[p.handle for p in self.plans])
+        pi = (ctypes.c_int * max(1, n))(*[int(i) for i in plan_index])
+        of = (ctypes.c_int64 * max(1, n))(*[int(o) for o in offsets])
+        self.handle = ctypes.c_void_p()
+        _check(lib.sht_uneven_create(hs, len(self.plans), n, pi, of, ctypes.byref(self.handle)))
+
+    def _run(self, name, x, out, stream):
+        if x.dtype != torch.complex128 or not x.is_cuda:
+            raise ValueError("uneven batches take complex128 CUDA tensors")
+        x = x.contiguous()
+        if out is None:
+            out = torch.zeros_like(x)
+        _check(getattr(load_library(), name)(self.handle, ctypes.c_void_p(x.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+        return out
+
+    def forward(self, samples, out=None, stream=None):
+        return self._run("sht_uneven_forward", samples, out, stream)
+
+    def inverse(self, coeffs, out=None, stream=None):
+        return self._run("sht_uneven_inverse", coeffs, out, stream)
+
+    def set_wait_limit(self, seconds):
+        _check(load_library().sht_uneven_set_wait_limit(self.handle, float(seconds)))
+
+    def check(self):
+        _check(load_library().sht_uneven_check(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.sht_uneven_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def forward_uneven(plans, plan_index, offsets, samples, out=None, stream=None):
