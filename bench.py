@@ -652,8 +652,12 @@ def run_uneven(args):
     Ls = [int(L) for L in synth.loguniform_bandlimits(args.uneven_n, args.uneven_lo, args.uneven_hi, 4)]
     distinct = sorted(set(Ls))
     t0 = time.time()
-    plans = [Plan(L, dtype=args.dtype) for L in distinct]
+    if args.table_free:   # float64 plans without their P~ tables; the launches regenerate P~
+        plans = [Plan(L, dtype="f64", keep_ptilde=False) for L in distinct]
+    else:
+        plans = [Plan(L, dtype=args.dtype) for L in distinct]
     plan_s = time.time() - t0
+    table_bytes = sum(p.info()["table_bytes"] for p in plans)
     index = [distinct.index(L) for L in Ls]
     offsets, pos = [], 0
     for L in Ls:
@@ -690,16 +694,18 @@ def run_uneven(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    # the same batch through the grouped per-plan calls (eager)
-    for _ in range(2):
+    # the same batch through the grouped per-plan calls (eager; not offered by table-free plans)
+    ms_grouped = None
+    for _ in range(0 if args.table_free else 2):
         forward_uneven(plans, index, offsets, inverse_uneven(plans, index, offsets, c))
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(max(1, args.steps // 2)):
-        forward_uneven(plans, index, offsets, inverse_uneven(plans, index, offsets, c))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_grouped = e0.elapsed_time(e1) / max(1, args.steps // 2)
+    if not args.table_free:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(max(1, args.steps // 2)):
+            forward_uneven(plans, index, offsets, inverse_uneven(plans, index, offsets, c))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_grouped = e0.elapsed_time(e1) / max(1, args.steps // 2)
     flops = sum(8.0 * L ** 3 for L in Ls)   # inverse 4 L^3 + forward 4 L^3 per signal (Sec. IV-C counts)
     line = {
         "metric": "uneven batch fwd+inv signals/s (one persistent launch per direction)",
@@ -708,9 +714,12 @@ def run_uneven(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{len(Ls)} complex signals, L log-uniform in [{args.uneven_lo}, {args.uneven_hi}] "
                                f"(seed 4), f_lm re/im iid U[-1,1]; inverse then forward",
-                   "distinct_L": len(distinct), "L_max": max(Ls), "plan_arithmetic": args.dtype,
+                   "distinct_L": len(distinct), "L_max": max(Ls),
+                   "plan_arithmetic": "f64, no P~ tables (regenerated by the recursion)" if args.table_free else args.dtype,
+                   "plan_table_bytes": table_bytes,
                    "launch": "one CUDA graph per step: two cooperative launches"},
-        "grouped_calls": {"ms_per_step": ms_grouped, "value": len(Ls) / (ms_grouped * 1e-3)},
+        "grouped_calls": ({"ms_per_step": ms_grouped, "value": len(Ls) / (ms_grouped * 1e-3)}
+                          if ms_grouped else None),
         "roofline": {"bound": "alu", "kernel": "k_uneven_inverse + k_uneven_forward (float64 SIMT)",
                      "achieved": flops / (ms * 1e-3) / 1e12, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
                      "frac": flops / (ms * 1e-3) / 1e12 / FP64_TFLOPS_NOMINAL,
@@ -745,6 +754,9 @@ def main():
     ap.add_argument("--uneven-n", type=int, default=512)
     ap.add_argument("--uneven-lo", type=int, default=32)
     ap.add_argument("--uneven-hi", type=int, default=256)
+    ap.add_argument("--table-free", action="store_true",
+                    help="uneven workload with float64 plans that keep no P~ table (needed to fit "
+                         "L up to 1024: the launches regenerate P~ by its recursion)")
     args = ap.parse_args()
     if args.uneven:
         run_uneven(args)

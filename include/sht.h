@@ -103,6 +103,12 @@ typedef enum {
 #define SHT_MEASURE_TAN13   4u   /* Theta^2: equal steps of |tan(theta)|^(1/3) dtheta              */
 #define SHT_MEASURE_MASK    6u
 
+/* Plan flag: keep no P~ table (L^3/2 doubles): it is built to invert the P_m and then freed.
+   Such plans (SHT_F64 only) serve the uneven-batch launches (sht_uneven_*), whose kernels
+   regenerate P~ by its recursion; every other transform entry point returns SHT_ERR_UNSUPPORTED
+   for them.  Cuts a plan's tables from 5/6 L^3 to 1/3 L^3 doubles. */
+#define SHT_PLAN_NO_PTILDE 8u
+
 #define SHT_MAX_L 2048   /* longest ring 4095: its chirp-z length 8192 fits one SM */
 
 /*
@@ -124,7 +130,8 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out);
 /*
  * sht_plan_with_thetas - as sht_plan, with the L ring co-latitudes given by the caller (host
  *   array of L doubles, theta_host[k] = theta_k in radians, any values in [0, pi] (to within
- *   1e-12) for which every P_m is invertible; Remark 1).  The ordering bits of `flags` are ignored.
+ *   1e-12) for which every P_m is invertible; Remark 1).  The ordering and measure bits of `flags`
+ *   are ignored; SHT_PLAN_NO_PTILDE applies.
  */
 sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host, uint32_t flags,
                                 sht_plan_t *out);

@@ -40,6 +40,9 @@ sht_status check_plan(sht_plan_t p) {
 sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch) {
     sht_status st = check_plan(p);
     if (st != SHT_OK) return st;
+    if (!p->pt)
+        return set_error(SHT_ERR_UNSUPPORTED, "the plan keeps no P~ table (SHT_PLAN_NO_PTILDE): only the "
+                                              "uneven-batch launches (sht_uneven_*) take it");
     if (batch < 0 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [0, 65535]");
     if (batch == 0) return SHT_OK;
     if (!in || !out) return set_error(SHT_ERR_INVALID_ARG, "NULL buffer");
@@ -76,6 +79,7 @@ void destroy(sht_plan_t p) {
     cudaGetDevice(&dev);
     if (dev != p->device) cudaSetDevice(p->device);
     cudaFree(p->d_theta); cudaFree(p->pt); cudaFree(p->pinv); cudaFree(p->pt2); cudaFree(p->pinv2);
+    cudaFree(p->sect_mant); cudaFree(p->sect_expo); cudaFree(p->rec_a); cudaFree(p->rec_b);
     cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
     cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
     cudaFree(p->d_tmaps);
@@ -187,7 +191,7 @@ sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
 }
 
 sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, double order_s,
-                      sht_plan_t *out, int spin = 0) {
+                      sht_plan_t *out, int spin = 0, bool keep_ptilde = true) {
     auto t0 = std::chrono::steady_clock::now();
     sht_plan_t p = new sht_plan_s;
     p->L = L;
@@ -236,6 +240,24 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
         else if (e != cudaSuccess)
             st = cuda_check(e, "per-order inverses");
     }
+    uint64_t rec_bytes = 0;
+    if (st == SHT_OK && spin == 0) {
+        // what regenerates P~ on the fly: sectoral start values and recursion coefficients
+        const size_t LL = (size_t)L * L, R = (size_t)rows_total(L);
+        if ((e = cudaMalloc(&p->sect_mant, sizeof(double) * LL)) != cudaSuccess ||
+            (e = cudaMalloc(&p->sect_expo, sizeof(int) * LL)) != cudaSuccess ||
+            (e = cudaMalloc(&p->rec_a, sizeof(double) * R)) != cudaSuccess ||
+            (e = cudaMalloc(&p->rec_b, sizeof(double) * R)) != cudaSuccess ||
+            (e = sectoral_values(L, p->d_theta, L, p->sect_mant, p->sect_expo, s)) != cudaSuccess ||
+            (e = recursion_coeffs(L, p->rec_a, p->rec_b, s)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(s)) != cudaSuccess)
+            st = cuda_check(e, "recursion data");
+        rec_bytes = (sizeof(double) + sizeof(int)) * LL + 2 * sizeof(double) * R;
+    }
+    if (st == SHT_OK && !keep_ptilde) {   // SHT_PLAN_NO_PTILDE: the inverses are built; drop P~
+        cudaFree(p->pt);
+        p->pt = nullptr;
+    }
     if (st == SHT_OK) {
         e = dft_plan_create(L, p->dft, dft_bytes, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -268,7 +290,8 @@ sht_status build_plan(int L, sht_dtype dtype, const std::vector<double> &theta, 
     if (st == SHT_OK && tensor_plan(p)) st = build_tensor_tables(p, s, tc_bytes);
     cudaStreamDestroy(s);
     if (st != SHT_OK) { destroy(p); *out = nullptr; return st; }
-    p->table_bytes = (spin ? 2 : 1) * (pt_bytes + pi_bytes) + dft_bytes + tc_bytes + f32_bytes + sizeof(double) * L;
+    p->table_bytes = (spin ? 2 : 1) * ((p->pt ? pt_bytes : 0) + pi_bytes) + dft_bytes + tc_bytes + f32_bytes +
+                     rec_bytes + sizeof(double) * L;
     p->plan_seconds = order_s + std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     *out = p;
     return SHT_OK;
@@ -713,17 +736,18 @@ const char *sht_last_error_message(void) { return g_error.c_str(); }
 
 sht_status sht_plan_with_thetas(int L, sht_dtype dtype, const double *theta_host, uint32_t flags,
                                 sht_plan_t *out) {
-    (void)flags;
     if (!out) return set_error(SHT_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
     if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
     if (!theta_host) return set_error(SHT_ERR_INVALID_ARG, "theta_host is NULL");
+    const bool keep = !(flags & SHT_PLAN_NO_PTILDE);
+    if (!keep && dtype != SHT_F64) return set_error(SHT_ERR_UNSUPPORTED, "SHT_PLAN_NO_PTILDE takes SHT_F64 plans");
     std::vector<double> th(theta_host, theta_host + L);
     // the equiangular set's end point pi (2L-1)/(2L-1) may round one ulp past pi: allow 1e-12
     for (double t : th)
         if (!(t >= -1e-12 && t <= M_PI + 1e-12)) return set_error(SHT_ERR_INVALID_ARG, "theta outside [0, pi]");
-    return build_plan(L, dtype, th, 0.0, out);
+    return build_plan(L, dtype, th, 0.0, out, 0, keep);
 }
 
 }  // extern "C"
@@ -770,11 +794,13 @@ sht_status sht_plan(int L, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {
     *out = nullptr;
     if (L < 1 || L > kMaxL) return set_error(SHT_ERR_UNSUPPORTED, "L must be in [1, 2048]");
     if ((int)dtype < 0 || (int)dtype > SHT_F32) return set_error(SHT_ERR_UNSUPPORTED, "dtype not supported");
+    const bool keep = !(flags & SHT_PLAN_NO_PTILDE);
+    if (!keep && dtype != SHT_F64) return set_error(SHT_ERR_UNSUPPORTED, "SHT_PLAN_NO_PTILDE takes SHT_F64 plans");
     std::vector<double> th;
     double order_s = 0.0;
     sht_status st = ordered_rings(L, flags, th, order_s);
     if (st != SHT_OK) return st;
-    return build_plan(L, dtype, th, order_s, out);
+    return build_plan(L, dtype, th, order_s, out, 0, keep);
 }
 
 sht_status sht_plan_spin(int L, int spin, sht_dtype dtype, uint32_t flags, sht_plan_t *out) {

@@ -112,7 +112,34 @@ __global__ void __launch_bounds__(128) k_table(int L, const double *__restrict__
     }
 }
 
+// Recursion coefficients of every order, block m at rows_off(L, m), entry l - m for the step that
+// produces degree l (l >= m + 1): a = sqrt(2m+3), b = 0 for l = m + 1, else a_lm, b_lm above.
+__global__ void k_recursion_coeffs(int L, double *__restrict__ ra, double *__restrict__ rb) {
+    const int m = blockIdx.x;
+    const int n = L - m;
+    double *a = ra + rows_off(L, m), *b = rb + rows_off(L, m);
+    const double md = (double)m;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int l = m + j;
+        double av = 0.0, bv = 0.0;
+        if (l == m + 1) {
+            av = sqrt(2.0 * md + 3.0);
+        } else if (l >= m + 2) {
+            const double ld = (double)l, l1 = ld - 1.0;
+            av = sqrt((4.0 * ld * ld - 1.0) / (ld * ld - md * md));
+            bv = sqrt((l1 * l1 - md * md) / (4.0 * l1 * l1 - 1.0));
+        }
+        a[j] = av;
+        b[j] = bv;
+    }
+}
+
 }  // namespace
+
+cudaError_t recursion_coeffs(int L, double *ra, double *rb, cudaStream_t s) {
+    k_recursion_coeffs<<<L, 128, 0, s>>>(L, ra, rb);
+    return cudaGetLastError();
+}
 
 cudaError_t sectoral_values(int L, const double *d_theta_rows, int nrows, double *mant, int *expo,
                             cudaStream_t s) {

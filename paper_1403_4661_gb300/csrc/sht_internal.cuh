@@ -120,6 +120,11 @@ struct sht_plan_s {
     double *pt = nullptr;       // P~ table (spin plans: sP~^{+m})
     double *pinv = nullptr;     // per-order inverses (spin plans: of the +m matrices)
     int spin = 0;               // spin weight s of the plan's signals (Sec. III-H); 0: scalar
+    // scalar plans: what regenerates P~ on the fly (kernels that walk the recursion instead of
+    // reading pt): sectoral start values (L x L, order-major) and recursion coefficients
+    double *sect_mant = nullptr;
+    int *sect_expo = nullptr;
+    double *rec_a = nullptr, *rec_b = nullptr;
     double *pt2 = nullptr;      // spin plans: (-1)^m sP~^{-m}, layout of pt
     double *pinv2 = nullptr;    // spin plans: inverses of the -m matrices, layout of pinv
     float *ptF = nullptr;       // SHT_F32: the P~ table rounded to float32
@@ -183,6 +188,9 @@ cudaError_t build_ptilde_table(int L, const double *d_theta_rows, int nrows, dou
 // The sectoral values P~_m^m(theta_r) = mant[m * nrows + r] * 2^expo[m * nrows + r], m < L.
 cudaError_t sectoral_values(int L, const double *d_theta_rows, int nrows, double *mant, int *expo,
                             cudaStream_t s);
+// Recursion coefficients a_lm, b_lm of the table recursion, block m at rows_off(L, m), entry l - m
+// (the step producing degree l; a = sqrt(2m+3), b = 0 for l = m + 1).
+cudaError_t recursion_coeffs(int L, double *ra, double *rb, cudaStream_t s);
 
 // invert.cu: explicit inverses of P_m for every m >= m_first from the P~ table (blocks of
 // orders below m_first are left as they are).

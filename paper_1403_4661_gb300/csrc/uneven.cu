@@ -39,7 +39,10 @@ constexpr int kUThreads = 256;
 
 struct UPlan {
     int L, Mtab;
-    const double *pt, *pinv;                    // P~ table, per-order inverses (scalar layouts)
+    const double *pt, *pinv;                    // P~ table (null: regenerated), per-order inverses
+    const double *theta;                        // ring co-latitudes
+    const double *sect_mant; const int *sect_expo;   // P~_m^m(theta_k) = mant * 2^expo, [m][k]
+    const double *rec_a, *rec_b;                // recursion coefficients, block m at rows_off(L, m)
     const double2 *chirp, *filt, *tw;           // ring DFT tables
     const int *ring_M;                          // per ring: chirp-z length (0: direct)
     const int64_t *ring_foff;                   // per ring: filter offset
@@ -107,6 +110,45 @@ __device__ bool grid_barrier_once(const UArgs &a, int *flag) {
     return *flag != 0;
 }
 
+// sum_{l = m..L-1} P~_l^m(theta_k) v[l - m][0..3] with P~ regenerated by its recursion (Sec. III-G)
+// instead of read from a table: the sectoral start value is carried as mantissa * 2^e while it is
+// below the float64 range (values below 2^-960 contribute nothing and are skipped), then the
+// recursion continues on plain values (they only grow from there).  v: 4 doubles per degree.
+__device__ __forceinline__ void recur_dot(const UPlan &pl, int L, int m, int k, double xk, const double *v,
+                                          double &s0, double &s1, double &s2, double &s3) {
+    const int n = L - m;
+    double p = __ldg(pl.sect_mant + (int64_t)m * L + k), pp = 0.0;
+    int e = __ldg(pl.sect_expo + (int64_t)m * L + k);
+    const double *ra = pl.rec_a + rows_off(L, m), *rb = pl.rec_b + rows_off(L, m);
+    bool live = false;
+    s0 = s1 = s2 = s3 = 0.0;
+    for (int j = 0; j < n; ++j) {
+        if (j > 0) {
+            const double nx = __ldg(ra + j) * fma(xk, p, -__ldg(rb + j) * pp);
+            pp = p;
+            p = nx;
+        }
+        if (!live) {
+            const int be = (int)((__double_as_longlong(p) >> 52) & 0x7ff) - 1023;   // exponent of p
+            if (p != 0.0 && be + e >= -960) {
+                p = scalbn(p, e);
+                pp = scalbn(pp, e);
+                live = true;
+            } else if (e < 0 && be > 512) {   // keep the mantissa in range while e < 0
+                p = scalbn(p, -512);
+                pp = scalbn(pp, -512);
+                e += 512;
+            }
+        }
+        if (live) {
+            s0 = fma(p, v[4 * j], s0);
+            s1 = fma(p, v[4 * j + 1], s1);
+            s2 = fma(p, v[4 * j + 2], s2);
+            s3 = fma(p, v[4 * j + 3], s3);
+        }
+    }
+}
+
 // ---- inverse ----------------------------------------------------------------------------------
 
 // Bin t of ring k (2k+1 bins) folded from the signal's synthesis table G (rows (|m|, k), 4
@@ -147,17 +189,20 @@ __global__ void __launch_bounds__(kUThreads) k_uneven_inverse(UArgs a) {
             xs[4 * r] = p.x; xs[4 * r + 1] = p.y; xs[4 * r + 2] = q.x; xs[4 * r + 3] = q.y;
         }
         __syncthreads();
-        const double *P = pl.pt + pt_off(L, m);
         double *G = a.ws + sg.ws + (int64_t)m * L * 4;
         for (int k = tid; k < L; k += blockDim.x) {
-            const double *row = P + (int64_t)k * n;
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-            for (int r = 0; r < n; ++r) {
-                const double pv = __ldg(row + r);
-                s0 = fma(pv, xs[4 * r], s0);
-                s1 = fma(pv, xs[4 * r + 1], s1);
-                s2 = fma(pv, xs[4 * r + 2], s2);
-                s3 = fma(pv, xs[4 * r + 3], s3);
+            if (pl.pt) {
+                const double *row = pl.pt + pt_off(L, m) + (int64_t)k * n;
+                for (int r = 0; r < n; ++r) {
+                    const double pv = __ldg(row + r);
+                    s0 = fma(pv, xs[4 * r], s0);
+                    s1 = fma(pv, xs[4 * r + 1], s1);
+                    s2 = fma(pv, xs[4 * r + 2], s2);
+                    s3 = fma(pv, xs[4 * r + 3], s3);
+                }
+            } else {
+                recur_dot(pl, L, m, k, cos(__ldg(pl.theta + k)), xs, s0, s1, s2, s3);
             }
             double *g = G + 4 * (int64_t)k;
             g[0] = s0; g[1] = s1; g[2] = s2; g[3] = s3;
@@ -303,16 +348,19 @@ __global__ void __launch_bounds__(kUThreads) k_uneven_forward(UArgs a) {
             if (m == 0) break;
             __syncthreads();
             // Eqs. (15)-(16): G_{+-m}(theta_k), k < m, out of bins alias_k(+-m) of ring k
-            const double *Pt = pl.pt + pt_off(L, m);
             for (int k = tid; k < m; k += blockDim.x) {
-                const double *row = Pt + (int64_t)k * n;
                 double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                for (int r = 0; r < n; ++r) {
-                    const double pv = __ldg(row + r);
-                    s0 = fma(pv, fm[4 * r], s0);
-                    s1 = fma(pv, fm[4 * r + 1], s1);
-                    s2 = fma(pv, fm[4 * r + 2], s2);
-                    s3 = fma(pv, fm[4 * r + 3], s3);
+                if (pl.pt) {
+                    const double *row = pl.pt + pt_off(L, m) + (int64_t)k * n;
+                    for (int r = 0; r < n; ++r) {
+                        const double pv = __ldg(row + r);
+                        s0 = fma(pv, fm[4 * r], s0);
+                        s1 = fma(pv, fm[4 * r + 1], s1);
+                        s2 = fma(pv, fm[4 * r + 2], s2);
+                        s3 = fma(pv, fm[4 * r + 3], s3);
+                    }
+                } else {
+                    recur_dot(pl, L, m, k, cos(__ldg(pl.theta + k)), fm, s0, s1, s2, s3);
                 }
                 const int aa = alias_bin(m, k), o = aa < 0 ? -aa : aa;
                 double *w = W + (rows_off(L, o) + (k - o)) * 4;
@@ -448,7 +496,8 @@ sht_status sht_uneven_create(const sht_plan_t *plans, int nplans, int64_t nsig, 
     std::vector<UPlan> hp((size_t)nplans);
     for (int g = 0; g < nplans; ++g) {
         const sht_plan_t p = plans[g];
-        hp[(size_t)g] = UPlan{p->L, p->dft.Mtab, p->pt, p->pinv, p->dft.chirp, p->dft.filt, p->dft.twiddle,
+        hp[(size_t)g] = UPlan{p->L, p->dft.Mtab, p->pt, p->pinv, p->d_theta, p->sect_mant, p->sect_expo,
+                              p->rec_a, p->rec_b, p->dft.chirp, p->dft.filt, p->dft.twiddle,
                               p->dft.d_ring_M, p->dft.d_ring_foff};
     }
     std::vector<USig> hs((size_t)nsig);

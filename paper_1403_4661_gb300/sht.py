@@ -32,6 +32,7 @@ DTYPES = {"f64": SHT_F64, "f64_tensor": SHT_F64_TENSOR, "bf16_refined": SHT_BF16
 SHT_ORDER_GREEDY = 0
 SHT_ORDER_SIMPLE = 1
 MEASURES = {"uniform": 0, "sin": 2, "tan13": 4}   # SHT_MEASURE_* flags
+SHT_PLAN_NO_PTILDE = 8
 EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_bandlimit",
             "sht_plan_reserve", "sht_plan_destroy", "sht_forward", "sht_inverse",
             "sht_inverse_adjoint", "sht_forward_adjoint", "sht_get_info", "sht_status_string",
@@ -364,9 +365,11 @@ class Plan:
     Plan(L, measure="sin" | "tan13")  rings from the sets of the alternative measures (Sec. III-F)
     Plan(L, theta=array_of_L_values)  caller-given ring co-latitudes
     Plan(L, spin=s)                   spin-s functions (Sec. III-H), float64 only
+    Plan(L, keep_ptilde=False)        no P~ table (only uneven batches, which regenerate it)
     """
 
-    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64, measure="uniform", spin=0):
+    def __init__(self, L, theta=None, ordering="greedy", dtype=SHT_F64, measure="uniform", spin=0,
+                 keep_ptilde=True):
         self.L = int(L)
         dtype = DTYPES.get(dtype, dtype)
         self.dtype = dtype
@@ -374,11 +377,13 @@ class Plan:
         # element type of the plan's signals: complex64 for SHT_F32, complex128 otherwise
         self.cdtype = torch.complex64 if dtype == SHT_F32 else torch.complex128
         flags = {"greedy": SHT_ORDER_GREEDY, "simple": SHT_ORDER_SIMPLE}[ordering] | MEASURES[measure]
+        if not keep_ptilde:
+            flags |= SHT_PLAN_NO_PTILDE
         if self.spin != 0:
             self.handle = (sht_plan_spin_with_thetas(self.L, self.spin, theta, dtype) if theta is not None
                            else sht_plan_spin(self.L, self.spin, dtype, flags))
         elif theta is not None:
-            self.handle = sht_plan_with_thetas(self.L, theta, dtype)
+            self.handle = sht_plan_with_thetas(self.L, theta, dtype, flags & SHT_PLAN_NO_PTILDE)
         else:
             self.handle = sht_plan(self.L, dtype, flags)
         self.theta = sht_plan_thetas(self.handle, self.L)

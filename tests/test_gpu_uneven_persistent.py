@@ -116,3 +116,35 @@ def test_persistent_uneven_rejects_bad_layouts():
     with pytest.raises(SHTError, match="INVALID_ARG"):
         ub._run("sht_uneven_forward", x, x, None)  # input and output overlap
     ub.close()
+
+
+def test_table_free_plans_regenerate_ptilde():
+    """Plans made with SHT_PLAN_NO_PTILDE drop the L^3/2 P~ table; the persistent launches rebuild
+    P~ by its recursion and give the oracle's results, and agree with table-holding plans."""
+    from paper_1403_4661_gb300.sht import Plan, SHTError, UnevenBatch
+    Ls = [1, 2, 40, 130, 77, 130]
+    plans_t, index, offsets, coeffs, packed = _workload(Ls, 13, dtypes=("f64",))
+    distinct = sorted(set(Ls))
+    plans_f = [Plan(L, theta=oracle_thetas(L), keep_ptilde=False) for L in distinct]
+    assert plans_f[-1].info()["table_bytes"] < plans_t[-1].info()["table_bytes"]
+    c = torch.from_numpy(packed).to(DEV)
+    ut, uf = UnevenBatch(plans_t, index, offsets), UnevenBatch(plans_f, index, offsets)
+    s_t, s_f = ut.inverse(c), uf.inverse(c)
+    c_t, c_f = ut.forward(s_t), uf.forward(s_f)
+    uf.check()
+    scale = max(1.0, float(s_t.abs().max()))
+    assert float((s_f - s_t).abs().max()) <= 1e-13 * scale
+    assert float((c_f - c_t).abs().max()) <= 1e-12
+    s_h, c_h = s_f.cpu().numpy(), c_f.cpu().numpy()
+    for i, L in enumerate(Ls):
+        sl = slice(int(offsets[i]), int(offsets[i]) + L * L)
+        ref = osht.inverse(coeffs[i][None], L, oracle_thetas(L))[0]
+        assert np.abs(s_h[sl] - ref).max() <= tol_samples(ref), (i, L)
+        assert np.abs(c_h[sl] - coeffs[i]).max() <= 1e-11, (i, L)
+    # the batched entry points refuse a plan without its P~ table
+    with pytest.raises(SHTError, match="UNSUPPORTED"):
+        plans_f[-1].forward(torch.zeros((1, 130 * 130), dtype=torch.complex128, device=DEV))
+    with pytest.raises(SHTError, match="UNSUPPORTED"):
+        Plan(16, keep_ptilde=False, dtype="f64_tensor")
+    ut.close()
+    uf.close()
