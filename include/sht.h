@@ -213,6 +213,33 @@ sht_status sht_inverse(sht_plan_t plan, const void *d_coeffs, void *d_samples, i
                        void *stream);
 
 /*
+ * sht_ring_analysis - the forward ring DFTs alone (the first step of Procedure 1, Sec. III-C: the
+ *   DFT along each iso-latitude ring, Eq. (11)'s sum over phi).  d_samples: device, batch * L^2
+ *   complex, ring-major (ring k = 0..L-1 at offset k^2, sample n at phi = 2 pi n / (2k+1)).
+ *   d_bins: device, batch * L^2 complex, ring-major like the samples: bin j (|j| <= k) of ring k at
+ *   k^2 + k + j, holding (1/N_k) sum_n s_k[n] e^{-2 pi i j n / N_k}, N_k = 2k+1.  The 1/N_k makes
+ *   bin j the sum of the orders m = j mod N_k of the ring's G_m(theta_k) (Eq. (15)); the paper's
+ *   2 pi factor of Eq. (11) is left out, as in every entry point of this library.
+ *   The same kernels and launches as the ring-DFT step of sht_forward, followed by one layout
+ *   kernel (the forward keeps its bins order-major).  complex128 for every arithmetic but SHT_F32
+ *   (complex64, float32 DFTs).  Uses the plan's workspace (grown for batch as sht_forward does);
+ *   accepts plans made with SHT_PLAN_NO_PTILDE.  Errors: those of sht_forward's argument checks.
+ */
+sht_status sht_ring_analysis(sht_plan_t plan, const void *d_samples, void *d_bins, int64_t batch,
+                             void *stream);
+
+/*
+ * sht_ring_synthesis - the inverse ring DFTs alone (the last step of Procedure 2, Sec. III-D,
+ *   Eq. (18)): s_k[n] = sum_{|j| <= k} B_k[j] e^{+2 pi i j n / N_k} from ring-major bins
+ *   (layout of sht_ring_analysis), so that sht_ring_synthesis(sht_ring_analysis(s)) = s.
+ *   Runs the inverse's fold + inverse-DFT kernels on a synthesis table that holds bin j of ring k
+ *   as order j (zero for |m| > k), after one layout kernel that writes that table.  Arithmetic,
+ *   workspace and errors as sht_ring_analysis.
+ */
+sht_status sht_ring_synthesis(sht_plan_t plan, const void *d_bins, void *d_samples, int64_t batch,
+                              void *stream);
+
+/*
  * sht_forward_uneven, sht_inverse_uneven - one transform direction over nsig signals of different
  *   band-limits (the per-signal transform is the paper's; batching signals of uneven L is ours).
  *   plans[0..nplans): plans created beforehand on the calling device, one per band-limit (any

@@ -11,6 +11,8 @@ Modules
   legendre  scaled associated Legendre functions P~_l^m(theta) = Y_l^m(theta, 0)   (Sec. III-G)
   sampling  ring layout, equiangular set, simple and greedy ring orderings        (Sec. III-A, III-E)
   sht       forward SHT (Procedure 1), inverse SHT (Procedure 2), dense system, adjoints
+  ring      ring DFTs and their inverses by direct sums                      (Eqs. (11), (18))
+  spin      spin-s transforms from the Wigner-d recursion                    (Sec. III-H, App. A)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against something other
 than itself (closed forms, scipy's Y_l^m, mpmath, orthonormality by Gauss-Legendre quadrature,

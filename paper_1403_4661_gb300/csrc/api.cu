@@ -37,10 +37,10 @@ sht_status check_plan(sht_plan_t p) {
     return SHT_OK;
 }
 
-sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch) {
+sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch, bool need_ptilde) {
     sht_status st = check_plan(p);
     if (st != SHT_OK) return st;
-    if (!p->pt)
+    if (need_ptilde && !p->pt)
         return set_error(SHT_ERR_UNSUPPORTED, "the plan keeps no P~ table (SHT_PLAN_NO_PTILDE): only the "
                                               "uneven-batch launches (sht_uneven_*) take it");
     if (batch < 0 || batch > kMaxBatch) return set_error(SHT_ERR_INVALID_ARG, "batch out of range [0, 65535]");
@@ -1108,6 +1108,44 @@ sht_status sht_inverse(sht_plan_t p, const void *d_coeffs, void *d_samples, int6
     return cuda_check(inverse_impl(p, p->ws, (const double2 *)d_coeffs, (double2 *)d_samples, batch,
                                    (cudaStream_t)stream),
                       "sht_inverse");
+}
+
+sht_status sht_ring_analysis(sht_plan_t p, const void *d_samples, void *d_bins, int64_t batch, void *stream) {
+    sht_status st = check_io(p, d_samples, d_bins, batch, false);   // ring DFTs only: no P~
+    if (st != SHT_OK || batch == 0) return st;
+    if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (p->dtype == SHT_F32) {
+        float *W = reinterpret_cast<float *>(p->ws.a);
+        e = ring_dft_to_bins(p->L, p->dft, (const float2 *)d_samples, W, batch, true, s);
+        if (e == cudaSuccess) e = bins_to_rings(p->L, batch, W, (float2 *)d_bins, s);
+    } else {
+        double *W = p->ws.a;
+        e = ring_dft_to_bins(p->L, p->dft, (const double2 *)d_samples, W, batch, true, s);
+        if (e == cudaSuccess) e = bins_to_rings(p->L, batch, W, (double2 *)d_bins, s);
+    }
+    p->launches += 1 + dft_launches(p->dft);
+    return cuda_check(e, "sht_ring_analysis");
+}
+
+sht_status sht_ring_synthesis(sht_plan_t p, const void *d_bins, void *d_samples, int64_t batch, void *stream) {
+    sht_status st = check_io(p, d_bins, d_samples, batch, false);
+    if (st != SHT_OK || batch == 0) return st;
+    if ((st = ensure_workspace(p, batch)) != SHT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    if (p->dtype == SHT_F32) {
+        float *G = reinterpret_cast<float *>(p->ws.g);
+        e = rings_to_table(p->L, batch, (const float2 *)d_bins, G, s);
+        if (e == cudaSuccess) e = fold_ring_idft(p->L, p->dft, G, (float2 *)d_samples, batch, s);
+    } else {
+        double *G = p->ws.g;
+        e = rings_to_table(p->L, batch, (const double2 *)d_bins, G, s);
+        if (e == cudaSuccess) e = fold_ring_idft(p->L, p->dft, G, (double2 *)d_samples, batch, s);
+    }
+    p->launches += 1 + dft_launches(p->dft);
+    return cuda_check(e, "sht_ring_synthesis");
 }
 
 sht_status sht_forward_uneven(const sht_plan_t *plans, int nplans, int64_t nsig, const int *plan_index,

@@ -112,6 +112,43 @@ __global__ void k_update_max(int64_t n, double2 *__restrict__ x, const double2 *
     }
 }
 
+// Ring-major bins (per signal: bin j of ring k at k^2 + k + j, |j| <= k) from the order-major bins
+// W (bin q of ring k: block |q|, row k - |q|, slot 0 for q >= 0, 2 for q < 0).  Thread = one bin.
+template <typename T>
+__global__ void k_bins_to_rings(int L, int64_t batch, const T *__restrict__ W, cplx_t<T> *__restrict__ bins) {
+    const int64_t L2 = (int64_t)L * L;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L2 * batch) return;
+    const int64_t b = t / L2, idx = t - b * L2;
+    int k, j;
+    decode(idx, k, j);
+    const int o = j < 0 ? -j : j;
+    const T *w = W + (rows_off(L, o) + (k - o)) * (4 * batch) + 4 * b + (j < 0 ? 2 : 0);
+    bins[t] = mk2<T>(w[0], w[1]);
+}
+
+// Synthesis table Gt (row m L + k, columns 4b + 2s + c) holding ring k's bins as orders:
+// G_{+m}(theta_k) = bin +m, G_{-m}(theta_k) = bin -m for m <= k, zero for m > k, so that the fold
+// of Eq. (18) gives back the bins.  Thread = (row, signal), signal fastest: the four values of a
+// row's signals are written side by side.
+template <typename T>
+__global__ void k_rings_to_table(int L, int64_t batch, const cplx_t<T> *__restrict__ bins, T *__restrict__ Gt) {
+    const int64_t L2 = (int64_t)L * L;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L2 * batch) return;
+    const int64_t row = t / batch, b = t - row * batch;
+    const int m = (int)(row / L), k = (int)(row - (int64_t)m * L);
+    T v[4] = {0, 0, 0, 0};
+    if (m <= k) {
+        const cplx_t<T> *r = bins + b * L2 + (int64_t)k * k + k;
+        v[0] = r[m].x; v[1] = r[m].y;
+        if (m > 0) { v[2] = r[-m].x; v[3] = r[-m].y; }
+    }
+    T *g = Gt + row * (4 * batch) + 4 * b;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) g[q] = v[q];
+}
+
 }  // namespace
 
 cudaError_t residual(int64_t n, const double2 *s_in, double2 *r, cudaStream_t s) {
@@ -170,6 +207,32 @@ cudaError_t table_to_f32(const double *in, float *out, int64_t n, cudaStream_t s
     if (n <= 0) return cudaSuccess;
     k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, out, n);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t bins_to_rings_t(int L, int64_t batch, const T *W, cplx_t<T> *bins, cudaStream_t s) {
+    const int64_t n = (int64_t)L * L * batch;
+    k_bins_to_rings<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, W, bins);
+    return cudaGetLastError();
+}
+cudaError_t bins_to_rings(int L, int64_t batch, const double *W, double2 *bins, cudaStream_t s) {
+    return bins_to_rings_t<double>(L, batch, W, bins, s);
+}
+cudaError_t bins_to_rings(int L, int64_t batch, const float *W, float2 *bins, cudaStream_t s) {
+    return bins_to_rings_t<float>(L, batch, W, bins, s);
+}
+
+template <typename T>
+cudaError_t rings_to_table_t(int L, int64_t batch, const cplx_t<T> *bins, T *Gt, cudaStream_t s) {
+    const int64_t n = (int64_t)L * L * batch;
+    k_rings_to_table<T><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(L, batch, bins, Gt);
+    return cudaGetLastError();
+}
+cudaError_t rings_to_table(int L, int64_t batch, const double2 *bins, double *Gt, cudaStream_t s) {
+    return rings_to_table_t<double>(L, batch, bins, Gt, s);
+}
+cudaError_t rings_to_table(int L, int64_t batch, const float2 *bins, float *Gt, cudaStream_t s) {
+    return rings_to_table_t<float>(L, batch, bins, Gt, s);
 }
 
 }  // namespace sht

@@ -177,9 +177,10 @@ sht_status cuda_check(cudaError_t e, const char *what);
 // Largest batch of one call: the batch is a grid dimension of the ring kernels.
 constexpr int64_t kMaxBatch = 65535;
 // Argument checks shared by the entry points (api.cu): plan non-NULL and on the current device;
-// batch in [0, kMaxBatch]; for batch > 0, non-NULL buffers aligned to one element and disjoint.
+// batch in [0, kMaxBatch]; for batch > 0, non-NULL buffers aligned to one element and disjoint;
+// with need_ptilde, a plan that keeps its P~ table (every transform but the ring stages).
 sht_status check_plan(sht_plan_t p);
-sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch);
+sht_status check_io(sht_plan_t p, const void *in, const void *out, int64_t batch, bool need_ptilde = true);
 
 // legendre.cu: P~ table for arbitrary co-latitudes (rows), all orders.
 cudaError_t build_ptilde_table(int L, const double *d_theta_rows, int nrows, double *d_table,
@@ -288,6 +289,12 @@ cudaError_t orders_to_coeffs(int L, int64_t batch, const double *X, double2 *coe
                              cudaStream_t s);
 cudaError_t coeffs_to_orders(int L, int64_t batch, const float2 *coeffs, float *X, cudaStream_t s);
 cudaError_t orders_to_coeffs(int L, int64_t batch, const float *X, float2 *coeffs, cudaStream_t s);
+// ring-major bins (k^2 + k + j) from the order-major bins W; and ring-major bins placed in a
+// synthesis table Gt as orders |m| <= k (zero elsewhere), the input of fold_ring_idft
+cudaError_t bins_to_rings(int L, int64_t batch, const double *W, double2 *bins, cudaStream_t s);
+cudaError_t bins_to_rings(int L, int64_t batch, const float *W, float2 *bins, cudaStream_t s);
+cudaError_t rings_to_table(int L, int64_t batch, const double2 *bins, double *Gt, cudaStream_t s);
+cudaError_t rings_to_table(int L, int64_t batch, const float2 *bins, float *Gt, cudaStream_t s);
 // n float64 values rounded to float32 (tables of SHT_F32 plans)
 cudaError_t table_to_f32(const double *in, float *out, int64_t n, cudaStream_t s);
 // refinement: r = s - r (n complex values); x += dx and max |Re, Im dx| into *mx

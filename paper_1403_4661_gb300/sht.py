@@ -41,7 +41,8 @@ EXPORTED = ["sht_plan", "sht_plan_with_thetas", "sht_plan_thetas", "sht_plan_ban
             "sht_forward_uneven", "sht_inverse_uneven", "sht_plan_set_wait_limit",
             "sht_plan_set_paths", "sht_plan_autotune", "sht_plan_save", "sht_plan_load",
             "sht_plan_spin", "sht_plan_spin_with_thetas", "sht_uneven_create", "sht_uneven_forward",
-            "sht_uneven_inverse", "sht_uneven_set_wait_limit", "sht_uneven_check", "sht_uneven_destroy"]
+            "sht_uneven_inverse", "sht_uneven_set_wait_limit", "sht_uneven_check", "sht_uneven_destroy",
+            "sht_ring_analysis", "sht_ring_synthesis"]
 SHT_PATH_DEFAULT = 0
 SHT_PATH_TENSOR = 1
 SHT_PATH_SIMT = 2
@@ -94,7 +95,7 @@ def load_library(path=LIB_PATH):
     lib.sht_plan_reserve.argtypes = [P, i64]
     lib.sht_plan_destroy.argtypes = [P]
     for name in ("sht_forward", "sht_inverse", "sht_inverse_adjoint", "sht_forward_adjoint",
-                 "sht_forward_noalloc"):
+                 "sht_forward_noalloc", "sht_ring_analysis", "sht_ring_synthesis"):
         getattr(lib, name).argtypes = [P, P, P, i64, P]
     lib.sht_get_info.argtypes = [P, ctypes.POINTER(ShtInfo)]
     lib.sht_status_string.argtypes = [ctypes.c_int]
@@ -255,6 +256,22 @@ def sht_inverse(h, L, coeffs, out=None, stream=None, cdtype=torch.complex128):
     x = _as_batch(coeffs, L, "coeffs", cdtype)
     y = torch.empty_like(x) if out is None else out
     _call("sht_inverse", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+def sht_ring_analysis(h, L, samples, out=None, stream=None, cdtype=torch.complex128):
+    """Forward ring DFTs alone: ring-major bins, bin j of ring k at k^2 + k + j, 1/(2k+1) scaled."""
+    x = _as_batch(samples, L, "samples", cdtype)
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_ring_analysis", h, x, y, x.numel() // (L * L), stream)
+    return y
+
+
+def sht_ring_synthesis(h, L, bins, out=None, stream=None, cdtype=torch.complex128):
+    """Inverse ring DFTs alone (unscaled) from ring-major bins."""
+    x = _as_batch(bins, L, "bins", cdtype)
+    y = torch.empty_like(x) if out is None else out
+    _call("sht_ring_synthesis", h, x, y, x.numel() // (L * L), stream)
     return y
 
 
@@ -463,6 +480,12 @@ class Plan:
 
     def forward_adjoint(self, coeffs, out=None, stream=None):
         return sht_forward_adjoint(self.handle, self.L, coeffs, out, stream, self.cdtype)
+
+    def ring_analysis(self, samples, out=None, stream=None):
+        return sht_ring_analysis(self.handle, self.L, samples, out, stream, self.cdtype)
+
+    def ring_synthesis(self, bins, out=None, stream=None):
+        return sht_ring_synthesis(self.handle, self.L, bins, out, stream, self.cdtype)
 
     def inverse_adjoint(self, samples, out=None, stream=None):
         return sht_inverse_adjoint(self.handle, self.L, samples, out, stream, self.cdtype)
