@@ -652,10 +652,21 @@ def run_uneven(args):
     Ls = [int(L) for L in synth.loguniform_bandlimits(args.uneven_n, args.uneven_lo, args.uneven_hi, 4)]
     distinct = sorted(set(Ls))
     t0 = time.time()
-    if args.table_free:   # float64 plans without their P~ tables; the launches regenerate P~
-        plans = [Plan(L, dtype="f64", keep_ptilde=False) for L in distinct]
-    else:
-        plans = [Plan(L, dtype=args.dtype) for L in distinct]
+    plans, cached = [], 0
+    for L in distinct:
+        # --plan-cache: the greedy co-latitudes of an earlier run (the ordering is deterministic),
+        # so that only the tables are rebuilt
+        path = os.path.join(args.plan_cache, f"thetas_L{L}.npy") if args.plan_cache else None
+        theta = np.load(path) if path and os.path.exists(path) else None
+        cached += theta is not None
+        if args.table_free:   # float64 plans without their P~ tables; the launches regenerate P~
+            pl = Plan(L, theta=theta, dtype="f64", keep_ptilde=False)
+        else:
+            pl = Plan(L, theta=theta, dtype=args.dtype)
+        if path and theta is None:
+            os.makedirs(args.plan_cache, exist_ok=True)
+            np.save(path, pl.theta)
+        plans.append(pl)
     plan_s = time.time() - t0
     table_bytes = sum(p.info()["table_bytes"] for p in plans)
     index = [distinct.index(L) for L in Ls]
@@ -667,6 +678,7 @@ def run_uneven(args):
     c = torch.from_numpy(packed).to(dev)
     s, c2 = torch.zeros_like(c), torch.zeros_like(c)
     ub = UnevenBatch(plans, index, offsets)
+    ub.set_wait_limit(30.0)   # one phase of a large batch can take over a second
     stream = torch.cuda.current_stream()
 
     def step():
@@ -694,6 +706,16 @@ def run_uneven(args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    # the two launches apart (eager, one step): where the step's time goes
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    ub.inverse(c, out=s)
+    ev[1].record(stream)
+    ub.forward(s, out=c2)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    ub.check()
+    ms_dir = {"inverse_ms": ev[0].elapsed_time(ev[1]), "forward_ms": ev[1].elapsed_time(ev[2])}
     # the same batch through the grouped per-plan calls (eager; not offered by table-free plans)
     ms_grouped = None
     for _ in range(0 if args.table_free else 2):
@@ -716,8 +738,9 @@ def run_uneven(args):
                                f"(seed 4), f_lm re/im iid U[-1,1]; inverse then forward",
                    "distinct_L": len(distinct), "L_max": max(Ls),
                    "plan_arithmetic": "f64, no P~ tables (regenerated by the recursion)" if args.table_free else args.dtype,
-                   "plan_table_bytes": table_bytes,
+                   "plan_table_bytes": table_bytes, "plans_from_cache": cached,
                    "launch": "one CUDA graph per step: two cooperative launches"},
+        "directions": ms_dir,
         "grouped_calls": ({"ms_per_step": ms_grouped, "value": len(Ls) / (ms_grouped * 1e-3)}
                           if ms_grouped else None),
         "roofline": {"bound": "alu", "kernel": "k_uneven_inverse + k_uneven_forward (float64 SIMT)",
@@ -754,6 +777,9 @@ def main():
     ap.add_argument("--uneven-n", type=int, default=512)
     ap.add_argument("--uneven-lo", type=int, default=32)
     ap.add_argument("--uneven-hi", type=int, default=256)
+    ap.add_argument("--plan-cache", default=None,
+                    help="uneven workload: directory of ring co-latitudes per L, read when present "
+                         "and written otherwise (skips the greedy ordering on later runs)")
     ap.add_argument("--table-free", action="store_true",
                     help="uneven workload with float64 plans that keep no P~ table (needed to fit "
                          "L up to 1024: the launches regenerate P~ by its recursion)")

@@ -275,14 +275,17 @@ sht_status sht_inverse_uneven(const sht_plan_t *plans, int nplans, int64_t nsig,
  *   sht_uneven_forward / sht_uneven_inverse - the whole batch in ONE cooperative launch whose CTAs
  *     stay resident and walk its work items: inverse = synthesis per (signal, order), one grid
  *     barrier, fold + inverse ring DFT per (signal, ring); forward = ring DFT per (signal, ring),
- *     one grid barrier, then each signal's order chain (solves and alias subtractions, m = L-1..0)
- *     on one CTA, largest L first.  float64 SIMT arithmetic on the plans' float64 tables (results
+ *     one grid barrier, then each signal's order chain (solves and alias subtractions, m = L-1..0):
+ *     the signals whose chain is a large share of the batch on teams of up to 16 CTAs (bounded
+ *     team barriers, two per order), the others on one CTA each, largest L first.  Plans made with
+ *     SHT_PLAN_NO_PTILDE have P~ regenerated by its recursion inside the launches.  float64 SIMT
+ *     arithmetic on the plans' float64 tables (results
  *     float64-accurate, as the batched calls).  Device buffers 16-byte aligned, input and output
  *     disjoint.  Stream-ordered; allocates nothing and never synchronises (capturable in a CUDA
  *     graph); calls on one batch object must not overlap in time (they share its scratch).
- *   sht_uneven_set_wait_limit - limit (1e-9 .. 60 s; default: that of plans[0]) of the grid
- *     barrier's wait; a CTA that reaches it abandons the call (results invalid) and sets the
- *     batch's status word.
+ *   sht_uneven_set_wait_limit - limit (1e-9 .. 60 s; default: that of plans[0]) of each wait on
+ *     other CTAs (the grid barrier, the team barriers); a CTA that reaches it abandons the call
+ *     (results invalid) and sets the batch's status word.
  *   sht_uneven_check - synchronise the device and report SHT_ERR_TIMEOUT if a barrier gave up
  *     since the last check (clears the flag).
  *   sht_uneven_destroy - free the batch object (synchronises the device; the plans are not freed).

@@ -12,17 +12,19 @@
 //                     the inverse ring DFT (Eq. (18)), with the plan's chirp-z tables;
 //   forward  phase 1: items (signal i, ring k): ring DFT into the signal's order-major bins;
 //            grid barrier;
-//            phase 2: items = signals, largest L first: one CTA runs a signal's whole order chain,
-//                     m = L-1..0, solve (plan's P_m^{-1}) and alias subtraction (plan's P~ block m),
-//                     with block-level synchronisation only.
+//            phase 2: each signal's order chain, m = L-1..0, solve (plan's P_m^{-1}) and alias
+//                     subtraction (plan's P~ block m, or P~ regenerated): the signals whose chain
+//                     is a large share of the batch on teams of up to 16 CTAs (rows and rings
+//                     split, two team barriers per order), the rest one CTA each, largest L
+//                     first, from a queue.
 //
 // All arithmetic is float64 on the SIMT pipes, on the plans' float64 tables (every complex128
-// scalar plan keeps them).  Items of one phase are independent; the only grid-wide wait is the
-// barrier between the phases, which is bounded (the plan wait limit of the first plan): a CTA that
-// gives up sets the batch's status word and an abort word, and every CTA leaves.  The cooperative
-// launch guarantees that all CTAs are resident, so the barrier cannot wait on a CTA that never
-// runs.  Scratch (bins or synthesis table per signal) is allocated by sht_uneven_create; a call
-// allocates nothing and synchronises nothing.
+// scalar plan keeps them).  Items of one phase are independent; the waits on other CTAs are the
+// grid barrier between the phases and the team barriers, all bounded (the plan wait limit of the
+// first plan): a CTA that gives up sets the batch's status word and an abort word, and every CTA
+// leaves.  The cooperative launch guarantees that all CTAs are resident, so no barrier can wait on
+// a CTA that never runs.  Scratch (bins or synthesis table per signal) is allocated by
+// sht_uneven_create; a call allocates nothing and synchronises nothing.
 #include <algorithm>
 #include <cstring>
 #include <numeric>
@@ -55,10 +57,19 @@ struct USig {
     int64_t item0;    // first item of the signal in the per-(signal, order / ring) phases
 };
 
+// One member's share of a team chain: signal, rank in the team, team size, team index.
+struct UTask {
+    int sig, rank, T, team;
+};
+
 struct UArgs {
     const UPlan *plans;
     const USig *sigs;
-    const int *lpt;   // signal indices by descending L
+    const UTask *tasks;      // team tasks, CTA c: tasks[task_start[c] .. task_start[c+1])
+    const int *task_start;   // gridDim.x + 1 entries
+    const int *small;        // signals chained by one CTA, descending L
+    int nsmall;
+    unsigned *team_bar;      // team t's barrier counter at 32 t (zeroed per launch)
     int nsig;
     int64_t items;    // sum of L_i
     double *ws;
@@ -149,6 +160,31 @@ __device__ __forceinline__ void recur_dot(const UPlan &pl, int L, int m, int k, 
     }
 }
 
+__device__ __forceinline__ void warp_sum4(double &s0, double &s1, double &s2, double &s3) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s3 += __shfl_xor_sync(0xffffffffu, s3, o);
+    }
+}
+
+// sum_c row[c] v[4c .. 4c+3], c < n, by one warp (lanes over c, coalesced row reads), summed
+// across the warp: every lane returns the four sums.
+__device__ __forceinline__ void warp_dot4(const double *__restrict__ row, const double *v, int n, int lane,
+                                          double &s0, double &s1, double &s2, double &s3) {
+    s0 = s1 = s2 = s3 = 0.0;
+    for (int c = lane; c < n; c += 32) {
+        const double pv = __ldg(row + c);
+        s0 = fma(pv, v[4 * c], s0);
+        s1 = fma(pv, v[4 * c + 1], s1);
+        s2 = fma(pv, v[4 * c + 2], s2);
+        s3 = fma(pv, v[4 * c + 3], s3);
+    }
+    warp_sum4(s0, s1, s2, s3);
+}
+
 // ---- inverse ----------------------------------------------------------------------------------
 
 // Bin t of ring k (2k+1 bins) folded from the signal's synthesis table G (rows (|m|, k), 4
@@ -190,6 +226,19 @@ __global__ void __launch_bounds__(kUThreads) k_uneven_inverse(UArgs a) {
         }
         __syncthreads();
         double *G = a.ws + sg.ws + (int64_t)m * L * 4;
+        if (pl.pt && n >= 64) {
+            // one ring per warp, lanes along the table row (coalesced)
+            const int lane = tid & 31;
+            for (int k = tid >> 5; k < L; k += (int)blockDim.x >> 5) {
+                double s0, s1, s2, s3;
+                warp_dot4(pl.pt + pt_off(L, m) + (int64_t)k * n, xs, n, lane, s0, s1, s2, s3);
+                if (lane == 0) {
+                    double *g = G + 4 * (int64_t)k;
+                    g[0] = s0; g[1] = s1; g[2] = s2; g[3] = s3;
+                }
+            }
+            continue;
+        }
         for (int k = tid; k < L; k += blockDim.x) {
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
             if (pl.pt) {
@@ -269,6 +318,137 @@ __device__ __forceinline__ void store_bin_u(double *W, int L, int k, int t, doub
     if (q == 0) { w[2] = 0.0; w[3] = 0.0; }
 }
 
+// Barrier of the T CTAs of one team (counter `bar`, growing within a launch; the j-th barrier is
+// passed at j T arrivals); false once any CTA of the launch has given up.  T = 1: the CTA alone.
+__device__ bool team_barrier(const UArgs &a, unsigned *bar, int T, unsigned &target, int *flag) {
+    __syncthreads();
+    if (T == 1) return true;
+    target += (unsigned)T;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        atomicAdd(bar, 1u);
+        volatile unsigned *cnt = bar, *abort_w = a.bar + 32;
+        if (*cnt < target) {
+            const uint64_t t0 = now_ns();
+            while (*cnt < target) {
+                if (*abort_w) { ok = 0; break; }
+                if (now_ns() - t0 > a.wait_ns) {
+                    atomicOr(a.status, 2);
+                    atomicExch(a.bar + 32, 1u);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// Order chain of signal `sig` (Eqs. (14)-(16), m = L-1..0) as member `rank` of a team of T CTAs:
+// the member solves rows [rank n / T, (rank+1) n / T) of F_m = P_m^{-1} g_m and subtracts the
+// aliases of rings [rank m / T, (rank+1) m / T); F_m passes between members through global
+// scratch (the signal's scratch beyond its bins), with a team barrier after the solve and one
+// after the alias subtraction.  T = 1 keeps everything in the CTA.  Rows and rings of n >= 64
+// go one per warp (lanes along the row: coalesced table reads), shorter ones one per thread.
+__device__ bool chain_signal(const UArgs &a, int sig, int rank, int T, unsigned *bar, double *ds, int *flag) {
+    const USig sg = a.sigs[sig];
+    const UPlan pl = a.plans[sg.plan];
+    const int L = sg.L, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = (int)blockDim.x >> 5;
+    double *W = a.ws + sg.ws;
+    double *Fg = W + 4 * rows_total(L);   // F_m of the team (4 L doubles; the scratch holds 4 L^2)
+    double2 *co = a.out + sg.off;
+    double *g = ds, *fm = ds + 4 * L;
+    unsigned target = 0;
+    for (int m = L - 1; m >= 0; --m) {
+        const int n = L - m;
+        __syncthreads();
+        // g_m: bins +-m of rings k >= m (Eq. (11)), free of the orders above m by now
+        const double *Wm = W + rows_off(L, m) * 4;
+        for (int i = tid; i < 4 * n; i += blockDim.x) g[i] = __ldcg(Wm + i);   // written by other CTAs
+        __syncthreads();
+        // Eq. (14): rows r0..r1 of F_m = P_m^{-1} g_m; f_l^{+m} and f_l^{-m} = (-1)^m F^{-}
+        const double *Pi = pl.pinv + pinv_off(L, m);
+        const int r0 = (int)((int64_t)rank * n / T), r1 = (int)((int64_t)(rank + 1) * n / T);
+        double *F = T > 1 ? Fg : fm;
+        auto emit = [&](int r, double s0, double s1, double s2, double s3) {
+            F[4 * r] = s0; F[4 * r + 1] = s1; F[4 * r + 2] = s2; F[4 * r + 3] = s3;
+            const int l = m + r;
+            double2 *cl = co + (int64_t)l * l + l;
+            cl[m] = make_double2(s0, s1);
+            if (m > 0) cl[-m] = (m & 1) ? make_double2(-s2, -s3) : make_double2(s2, s3);
+        };
+        if (n >= 64) {
+            for (int r = r0 + warp; r < r1; r += nw) {
+                double s0, s1, s2, s3;
+                warp_dot4(Pi + (int64_t)r * n, g, n, lane, s0, s1, s2, s3);
+                if (lane == 0) emit(r, s0, s1, s2, s3);
+            }
+        } else {
+            for (int r = r0 + tid; r < r1; r += blockDim.x) {
+                const double *row = Pi + (int64_t)r * n;
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                for (int c = 0; c < n; ++c) {
+                    const double pv = __ldg(row + c);
+                    s0 = fma(pv, g[4 * c], s0);
+                    s1 = fma(pv, g[4 * c + 1], s1);
+                    s2 = fma(pv, g[4 * c + 2], s2);
+                    s3 = fma(pv, g[4 * c + 3], s3);
+                }
+                emit(r, s0, s1, s2, s3);
+            }
+        }
+        if (m == 0) break;
+        if (!team_barrier(a, bar, T, target, flag)) return false;
+        if (T > 1)
+            for (int i = tid; i < 4 * n; i += blockDim.x) fm[i] = __ldcg(Fg + i);
+        __syncthreads();
+        // Eqs. (15)-(16): G_{+-m}(theta_k), k < m, out of bins alias_k(+-m) of ring k
+        const int k0 = (int)((int64_t)rank * m / T), k1 = (int)((int64_t)(rank + 1) * m / T);
+        auto subtract = [&](int k, double s0, double s1, double s2, double s3) {
+            const int aa = alias_bin(m, k), o = aa < 0 ? -aa : aa;
+            double *w = W + (rows_off(L, o) + (k - o)) * 4;
+            if (aa == 0) {
+                w[0] = __ldcg(w) - (s0 + s2);
+                w[1] = __ldcg(w + 1) - (s1 + s3);
+            } else {
+                const int sp = aa > 0 ? 0 : 2, sq = 2 - sp;   // slots of bins aa and -aa
+                w[sp] = __ldcg(w + sp) - s0; w[sp + 1] = __ldcg(w + sp + 1) - s1;
+                w[sq] = __ldcg(w + sq) - s2; w[sq + 1] = __ldcg(w + sq + 1) - s3;
+            }
+        };
+        if (pl.pt && n >= 64) {
+            for (int k = k0 + warp; k < k1; k += nw) {
+                double s0, s1, s2, s3;
+                warp_dot4(pl.pt + pt_off(L, m) + (int64_t)k * n, fm, n, lane, s0, s1, s2, s3);
+                if (lane == 0) subtract(k, s0, s1, s2, s3);
+            }
+        } else {
+            for (int k = k0 + tid; k < k1; k += blockDim.x) {
+                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+                if (pl.pt) {
+                    const double *row = pl.pt + pt_off(L, m) + (int64_t)k * n;
+                    for (int r = 0; r < n; ++r) {
+                        const double pv = __ldg(row + r);
+                        s0 = fma(pv, fm[4 * r], s0);
+                        s1 = fma(pv, fm[4 * r + 1], s1);
+                        s2 = fma(pv, fm[4 * r + 2], s2);
+                        s3 = fma(pv, fm[4 * r + 3], s3);
+                    }
+                } else {
+                    recur_dot(pl, L, m, k, cos(__ldg(pl.theta + k)), fm, s0, s1, s2, s3);
+                }
+                subtract(k, s0, s1, s2, s3);
+            }
+        }
+        if (!team_barrier(a, bar, T, target, flag)) return false;
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(kUThreads) k_uneven_forward(UArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     double2 *sm = reinterpret_cast<double2 *>(smem_raw);
@@ -312,68 +492,20 @@ __global__ void __launch_bounds__(kUThreads) k_uneven_forward(UArgs a) {
                   [&](int t, double2 v) { store_bin_u(W, L, k, t, v); });
     }
     if (!grid_barrier_once(a, &s_flag)) return;
-    // phase 2: one signal's order chain per CTA, largest L first
-    for (int idx = blockIdx.x; idx < a.nsig; idx += gridDim.x) {
-        const USig sg = a.sigs[a.lpt[idx]];
-        const UPlan pl = a.plans[sg.plan];
-        const int L = sg.L;
-        double *W = a.ws + sg.ws;
-        double2 *co = a.out + sg.off;
-        double *g = ds, *fm = ds + 4 * L;
-        for (int m = L - 1; m >= 0; --m) {
-            const int n = L - m;
-            __syncthreads();   // W holds the previous order's alias subtraction
-            // g_m: bins +-m of rings k >= m (Eq. (11)), free of the orders above m by now
-            const double *Wm = W + rows_off(L, m) * 4;
-            for (int i = tid; i < 4 * n; i += blockDim.x) g[i] = __ldcg(Wm + i);   // other CTAs wrote the bins
-            __syncthreads();
-            // Eq. (14): F_m = P_m^{-1} g_m; f_l^{+m} and f_l^{-m} = (-1)^m F^{-}
-            const double *Pi = pl.pinv + pinv_off(L, m);
-            for (int r = tid; r < n; r += blockDim.x) {
-                const double *row = Pi + (int64_t)r * n;
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                for (int cc = 0; cc < n; ++cc) {
-                    const double pv = __ldg(row + cc);
-                    s0 = fma(pv, g[4 * cc], s0);
-                    s1 = fma(pv, g[4 * cc + 1], s1);
-                    s2 = fma(pv, g[4 * cc + 2], s2);
-                    s3 = fma(pv, g[4 * cc + 3], s3);
-                }
-                fm[4 * r] = s0; fm[4 * r + 1] = s1; fm[4 * r + 2] = s2; fm[4 * r + 3] = s3;
-                const int l = m + r;
-                double2 *cl = co + (int64_t)l * l + l;
-                cl[m] = make_double2(s0, s1);
-                if (m > 0) cl[-m] = (m & 1) ? make_double2(-s2, -s3) : make_double2(s2, s3);
-            }
-            if (m == 0) break;
-            __syncthreads();
-            // Eqs. (15)-(16): G_{+-m}(theta_k), k < m, out of bins alias_k(+-m) of ring k
-            for (int k = tid; k < m; k += blockDim.x) {
-                double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-                if (pl.pt) {
-                    const double *row = pl.pt + pt_off(L, m) + (int64_t)k * n;
-                    for (int r = 0; r < n; ++r) {
-                        const double pv = __ldg(row + r);
-                        s0 = fma(pv, fm[4 * r], s0);
-                        s1 = fma(pv, fm[4 * r + 1], s1);
-                        s2 = fma(pv, fm[4 * r + 2], s2);
-                        s3 = fma(pv, fm[4 * r + 3], s3);
-                    }
-                } else {
-                    recur_dot(pl, L, m, k, cos(__ldg(pl.theta + k)), fm, s0, s1, s2, s3);
-                }
-                const int aa = alias_bin(m, k), o = aa < 0 ? -aa : aa;
-                double *w = W + (rows_off(L, o) + (k - o)) * 4;
-                if (aa == 0) {
-                    w[0] = __ldcg(w) - (s0 + s2);
-                    w[1] = __ldcg(w + 1) - (s1 + s3);
-                } else {
-                    const int sp = aa > 0 ? 0 : 2, sq = 2 - sp;   // slots of bins aa and -aa
-                    w[sp] = __ldcg(w + sp) - s0; w[sp + 1] = __ldcg(w + sp + 1) - s1;
-                    w[sq] = __ldcg(w + sq) - s2; w[sq + 1] = __ldcg(w + sq + 1) - s3;
-                }
-            }
-        }
+    // phase 2a: the large signals' chains, each on a team of CTAs (static lists, in one global
+    // order, so that a team only ever waits for members busy with earlier teams)
+    for (int t = a.task_start[blockIdx.x]; t < a.task_start[blockIdx.x + 1]; ++t) {
+        const UTask tk = a.tasks[t];
+        if (!chain_signal(a, tk.sig, tk.rank, tk.T, a.team_bar + 32 * tk.team, ds, &s_flag)) return;
+    }
+    // phase 2b: the other signals, one CTA each, largest L first from a shared queue
+    __shared__ int s_next;
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) s_next = (int)atomicAdd(a.bar + 64, 1u);
+        __syncthreads();
+        if (s_next >= a.nsmall) break;
+        chain_signal(a, a.small[s_next], 0, 1, nullptr, ds, &s_flag);
     }
 }
 
@@ -390,9 +522,13 @@ struct sht_uneven_s {
     std::vector<sht_plan_t> plans;
     UPlan *d_plans = nullptr;
     USig *d_sigs = nullptr;
-    int *d_lpt = nullptr;
+    UTask *d_tasks = nullptr;      // forward team tasks and their per-CTA ranges
+    int *d_task_start = nullptr;
+    int *d_small = nullptr;        // signals chained by one CTA, descending L
+    int nsmall = 0, nteams = 0;
+    unsigned *team_bar = nullptr;  // 32 words per team
     double *ws = nullptr;
-    unsigned *bar = nullptr;       // 64 words: arrival counter and abort word
+    unsigned *bar = nullptr;       // kBarWords words: arrival counter [0], abort word [32], queue [64]
     int *status = nullptr;
     size_t smem = 0;
     int grid_inv = 0, grid_fwd = 0;
@@ -404,9 +540,45 @@ namespace {
 
 void uneven_free(sht_uneven_t u) {
     if (!u) return;
-    cudaFree(u->d_plans); cudaFree(u->d_sigs); cudaFree(u->d_lpt); cudaFree(u->ws);
+    cudaFree(u->d_plans); cudaFree(u->d_sigs); cudaFree(u->d_tasks); cudaFree(u->d_task_start);
+    cudaFree(u->d_small); cudaFree(u->team_bar); cudaFree(u->ws);
     cudaFree(u->bar); cudaFree(u->status);
     delete u;
+}
+
+constexpr int kBarWords = 96;   // arrival counter [0], abort word [32], small-signal queue [64]
+constexpr int kMaxTeam = 16;    // CTAs of one team chain: two team barriers per order each
+
+// Forward phase 2's schedule.  The chain of a signal of band-limit L costs ~L^3; a signal whose
+// chain exceeds half a CTA's fair share of the batch (share = sum of L^3 over the grid) runs on a
+// team of T = min(16, ceil(2 L^3 / share)) CTAs (L >= 64), so that no task is much above half a
+// share and list scheduling stays within ~1.5 shares; the others run on one CTA each from a queue.
+// Teams, largest first, take consecutive CTAs, wrapping to CTA 0 when the grid is used up; every
+// CTA runs its team tasks in the order they were dealt, so a team waits only for members busy
+// with earlier teams.
+void plan_teams(const std::vector<USig> &hs, const std::vector<int> &lpt, int grid, std::vector<UTask> &tasks,
+                std::vector<int> &task_start, std::vector<int> &small, int &nteams) {
+    double total = 0.0;
+    for (const USig &sg : hs) total += (double)sg.L * sg.L * sg.L;
+    const double share = grid > 0 ? total / grid : 1.0;
+    std::vector<std::vector<UTask>> per((size_t)std::max(grid, 1));
+    int cursor = 0;
+    nteams = 0;
+    for (int i : lpt) {
+        const double w = (double)hs[(size_t)i].L * hs[(size_t)i].L * hs[(size_t)i].L;
+        int T = hs[(size_t)i].L >= 64 ? (int)std::min<double>(kMaxTeam, std::ceil(2.0 * w / share)) : 1;
+        T = std::min(T, grid);
+        if (T < 2) { small.push_back(i); continue; }
+        if (cursor + T > grid) cursor = 0;
+        for (int r = 0; r < T; ++r) per[(size_t)(cursor + r)].push_back(UTask{i, r, T, nteams});
+        cursor += T;
+        ++nteams;
+    }
+    task_start.assign((size_t)grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        task_start[(size_t)c + 1] = task_start[(size_t)c] + (int)per[(size_t)c].size();
+        tasks.insert(tasks.end(), per[(size_t)c].begin(), per[(size_t)c].end());
+    }
 }
 
 template <typename K>
@@ -434,9 +606,12 @@ sht_status uneven_launch(sht_uneven_t u, bool forward, const void *d_in, void *d
     const uintptr_t bytes = (uintptr_t)16 * (uintptr_t)u->span, a = (uintptr_t)d_in, b = (uintptr_t)d_out;
     if (a < b + bytes && b < a + bytes) return set_error(SHT_ERR_INVALID_ARG, "input and output overlap");
     cudaStream_t s = (cudaStream_t)stream;
-    UArgs args{u->d_plans, u->d_sigs, u->d_lpt, u->nsig, u->items, u->ws, u->bar, u->status, u->wait_ns,
+    UArgs args{u->d_plans, u->d_sigs, u->d_tasks, u->d_task_start, u->d_small, u->nsmall, u->team_bar,
+               u->nsig, u->items, u->ws, u->bar, u->status, u->wait_ns,
                (const double2 *)d_in, (double2 *)d_out};
-    if ((e = cudaMemsetAsync(u->bar, 0, 64 * sizeof(unsigned), s)) != cudaSuccess) return cuda_check(e, "uneven barrier");
+    if ((e = cudaMemsetAsync(u->bar, 0, kBarWords * sizeof(unsigned), s)) != cudaSuccess ||
+        (u->nteams && (e = cudaMemsetAsync(u->team_bar, 0, 32 * sizeof(unsigned) * (size_t)u->nteams, s)) != cudaSuccess))
+        return cuda_check(e, "uneven barrier");
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(forward ? u->grid_fwd : u->grid_inv));
     cfg.blockDim = dim3(kUThreads);
@@ -517,23 +692,36 @@ sht_status sht_uneven_create(const sht_plan_t *plans, int nplans, int64_t nsig, 
     u->smem = std::max({sizeof(double2) * (size_t)Mmax, sizeof(double) * 8 * (size_t)Lmax,
                         sizeof(double2) * (size_t)(2 * (2 * 31 + 1) + kUThreads + 2 * 63)});
     u->wait_ns = nplans > 0 ? plans[0]->wait_ns : 1000000000ull;
+    if ((e = coop_grid(k_uneven_inverse, u->smem, &u->grid_inv)) != cudaSuccess ||
+        (e = coop_grid(k_uneven_forward, u->smem, &u->grid_fwd)) != cudaSuccess) {
+        uneven_free(u);
+        return cuda_check(e, "uneven batch set-up");
+    }
+    std::vector<UTask> tasks;
+    std::vector<int> task_start, small;
+    plan_teams(hs, lpt, u->grid_fwd, tasks, task_start, small, u->nteams);
+    u->nsmall = (int)small.size();
     const size_t b_ws = sizeof(double) * (size_t)std::max<int64_t>(ws, 1);
     if ((e = cudaMalloc(&u->d_plans, sizeof(UPlan) * std::max<size_t>(hp.size(), 1))) != cudaSuccess ||
         (e = cudaMalloc(&u->d_sigs, sizeof(USig) * std::max<size_t>(hs.size(), 1))) != cudaSuccess ||
-        (e = cudaMalloc(&u->d_lpt, sizeof(int) * std::max<size_t>(lpt.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&u->d_tasks, sizeof(UTask) * std::max<size_t>(tasks.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&u->d_task_start, sizeof(int) * task_start.size())) != cudaSuccess ||
+        (e = cudaMalloc(&u->d_small, sizeof(int) * std::max<size_t>(small.size(), 1))) != cudaSuccess ||
+        (e = cudaMalloc(&u->team_bar, 32 * sizeof(unsigned) * (size_t)std::max(u->nteams, 1))) != cudaSuccess ||
         (e = cudaMalloc(&u->ws, b_ws)) != cudaSuccess ||
-        (e = cudaMalloc(&u->bar, 64 * sizeof(unsigned))) != cudaSuccess ||
+        (e = cudaMalloc(&u->bar, kBarWords * sizeof(unsigned))) != cudaSuccess ||
         (e = cudaMalloc(&u->status, sizeof(int))) != cudaSuccess) {
         uneven_free(u);
         return cuda_check(e, "uneven batch allocation");
     }
-    u->bytes = b_ws + sizeof(UPlan) * hp.size() + sizeof(USig) * hs.size() + sizeof(int) * lpt.size();
+    u->bytes = b_ws + sizeof(UPlan) * hp.size() + sizeof(USig) * hs.size() + sizeof(UTask) * tasks.size() +
+               sizeof(int) * (task_start.size() + small.size()) + 128 * (size_t)u->nteams;
     if ((nplans && (e = cudaMemcpy(u->d_plans, hp.data(), sizeof(UPlan) * hp.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
         (nsig && (e = cudaMemcpy(u->d_sigs, hs.data(), sizeof(USig) * hs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
-        (nsig && (e = cudaMemcpy(u->d_lpt, lpt.data(), sizeof(int) * lpt.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
-        (e = cudaMemset(u->status, 0, sizeof(int))) != cudaSuccess ||
-        (e = coop_grid(k_uneven_inverse, u->smem, &u->grid_inv)) != cudaSuccess ||
-        (e = coop_grid(k_uneven_forward, u->smem, &u->grid_fwd)) != cudaSuccess) {
+        (!tasks.empty() && (e = cudaMemcpy(u->d_tasks, tasks.data(), sizeof(UTask) * tasks.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemcpy(u->d_task_start, task_start.data(), sizeof(int) * task_start.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (!small.empty() && (e = cudaMemcpy(u->d_small, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice)) != cudaSuccess) ||
+        (e = cudaMemset(u->status, 0, sizeof(int))) != cudaSuccess) {
         uneven_free(u);
         return cuda_check(e, "uneven batch set-up");
     }

@@ -70,8 +70,9 @@ def test_persistent_uneven_agrees_with_grouped_calls_and_replays_in_a_graph():
     plans, index, offsets, coeffs, packed = _workload(Ls, 11)
     ub = UnevenBatch(plans, index, offsets)
     c = torch.from_numpy(packed).to(DEV)
-    s_ref = inverse_uneven(plans, index, offsets, c)
-    c_ref = forward_uneven(plans, index, offsets, s_ref)
+    # outputs zeroed first: the gaps between the signals are written by neither call
+    s_ref = inverse_uneven(plans, index, offsets, c, out=torch.zeros_like(c))
+    c_ref = forward_uneven(plans, index, offsets, s_ref, out=torch.zeros_like(c))
     s = torch.zeros_like(c)
     c2 = torch.zeros_like(c)
     ub.inverse(c, out=s)
