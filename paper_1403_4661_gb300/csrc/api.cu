@@ -83,7 +83,7 @@ void destroy(sht_plan_t p) {
     cudaFree(p->ptS); cudaFree(p->piS); cudaFree(p->ptE); cudaFree(p->piE);
     cudaFree(p->d_ptk_off); cudaFree(p->d_pik_off); cudaFree(p->d_status); cudaFree(p->d_refine_max);
     cudaFree(p->d_tmaps);
-    cudaFree(p->ptT); cudaFree(p->piT); cudaFree(p->d_tmaps_tf32);
+    cudaFree(p->ptT); cudaFree(p->piT); cudaFree(p->d_tmaps_tf32); cudaFree(p->chainQ);
     cudaFree(p->ptF); cudaFree(p->pinvF);
     dft_plan_destroy(p->dft);
     for (int st = 0; st < SHT_NUM_STAGES; ++st)
@@ -123,13 +123,14 @@ sht_status alloc_ws(sht_plan_t p, Workspace &w, int64_t batch) {
     }
     if (e == cudaSuccess && tensor_plan(p)) {
         const size_t xs = sizeof(__nv_bfloat16) * kTcSlices * Nc * (size_t)p->ptk_off[p->L];
-        const size_t words = sizeof(unsigned) * (size_t)tc_chain_words(batch);
+        const size_t words = sizeof(unsigned) * (size_t)tc_chain_words(p->L, batch);
+        const size_t sp2 = sizeof(double) * (size_t)kChainB * L * Nc;
         e = cudaMalloc(&w.xS, xs);
         if (e == cudaSuccess) e = cudaMalloc(&w.xE, sizeof(int) * Nc * L);
         if (e == cudaSuccess) e = cudaMalloc(&w.bar, words);
-        if (e == cudaSuccess) e = cudaMalloc(&w.part2, sp);
+        if (e == cudaSuccess) e = cudaMalloc(&w.part2, sp2);
         if (e == cudaSuccess) e = tc_x_tensor_maps(p->L, batch, w.xS, p->ptk_off, &w.tmX);
-        bytes += xs + sizeof(int) * Nc * L + words + sp + (uint64_t)p->L * kTensorMapBytes;
+        bytes += xs + sizeof(int) * Nc * L + words + sp2 + (uint64_t)p->L * kTensorMapBytes;
     }
     if (e != cudaSuccess) {
         free_ws(w);
@@ -173,6 +174,11 @@ sht_status build_tensor_tables(sht_plan_t p, cudaStream_t s, uint64_t &bytes) {
     if ((e = tc_table_tensor_maps(L, p->piS, p->pik_off, p->ptS, p->ptk_off, &p->d_tmaps)) != cudaSuccess)
         return cuda_check(e, "tensor maps of the table slices");
     bytes += (uint64_t)2 * L * kTensorMapBytes;
+    // Q_m = P~_m(rings of m's block below m) P_m^{-1}: the chain's tracked entries
+    const size_t qb = sizeof(double) * (size_t)kChainB * (size_t)rows_total(L);
+    if ((e = cudaMalloc(&p->chainQ, qb)) != cudaSuccess) return cuda_check(e, "chain table allocation");
+    if ((e = tc_chain_q_table(L, p->pt, p->pinv, p->chainQ, s)) != cudaSuccess) return cuda_check(e, "chain table");
+    bytes += qb;
     if (p->refine_tf32) {
         // TF32 copies of both tables for the low-precision chain, rows scaled like the slices
         const size_t ptt = sizeof(float) * (size_t)L * (size_t)p->ptk_off[L];
@@ -505,7 +511,7 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         Span sp(p, SHT_STAGE_SOLVE, s);
         const bool tf32 = p->refine_tf32 && nsl < kTcSlices;   // the TF32 refinement's F_lo
         const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off,
-                            tf32 ? p->d_tmaps_tf32 : p->d_tmaps};
+                            tf32 ? p->d_tmaps_tf32 : p->d_tmaps, p->chainQ};
         if (e == cudaSuccess)
             e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.part2, w.bar, p->d_status, nsl,
                                  tf32, p->chain_grid, p->wait_ns, s);

@@ -1,31 +1,41 @@
 // The forward's order chain (Procedure 1 in bin space, Eqs. (14)-(16)) on the tensor cores as ONE
-// persistent cooperative kernel.
+// persistent cooperative kernel, with the orders taken in blocks of kChainB.
 //
-// For m = L-1 .. 0 the chain solves F_m = P_m^{-1} g_m (g_m: bins +-m of rings k >= m, already free
-// of the orders above m) and subtracts the aliased contribution of orders +-m from the bins of the
-// rings k < m.  Each order depends on the one before (order m+1 aliases into ring m), so the
-// orders run strictly in sequence; per order the work is two small contractions, n x n and
-// m x n by n x 4B.  As separate launches each order costs several kernel starts, tensor-memory
-// allocations and mostly idle SMs; here one CTA per SM stays resident for the whole chain, keeps
-// its tensor memory and mbarriers, and the steps of an order are three phases separated by
-// grid-wide barriers:
-//     solve: tiles x K-splits of P_m^{-1} g_m (tcgen05 on exact BF16 slices)      | barrier
-//     sum of the solve's K-split partials -> F_m, f_l^{+-m}, column scales of F_m;
-//         order m+1's alias partials subtracted from the bins of rings k < m;
-//         column scales of g_{m-1} without its first row (rings >= m, final now)  | barrier
-//     alias: tiles x K-splits of P~_m(rings k < m) F_m                             | barrier
-// Order m's alias products reach ring m - 1, the first row of g_{m-1}, before they are summed
-// into the bins: the items of solve m - 1 add that row's partials up themselves (a few hundred
-// values), so no phase waits for the alias subtraction, which runs beside the next reduction.
-// The right-hand sides are read in float64 and cut into slices while they are staged in shared
+// For m = L-1 .. 0 the chain solves F_m = P_m^{-1} g_m (g_m: bins +-m of rings k = m + j >= m) and
+// subtracts the aliased contribution G_{+-m}(theta_k) = P~_m(theta_k) F_m of orders +-m from bins
+// alias_k(+-m) of the rings k < m.  Row j of g_m (ring m + j, bins +-m) is reached only by orders
+// m' = 2(m + j) + 1 - m = m + 2j + 1 and above (m' = +-m mod 2(m+j)+1 with m' > m + j).  So for a
+// block of orders [lo, hi] whose orders above hi are done, every row j >= J_m = floor((hi-m+1)/2)
+// of every g_m in the block is final already; only the J_m <= kChainB/2 leading rows ("tracked
+// entries", rings lo .. hi) still wait for orders of the same block.  Since G_{+-m'}(theta_k) =
+// Q_m'[k] g_m' with Q_m' = P~_m' P_m'^{-1} (plan table, rings lo <= k < m'), the tracked entries
+// follow from a small recurrence, and the block's heavy products run all at once.  Per block:
+//
+//   X1  (all CTAs, float64)  tracked entries: ring bins less the contributions of the block's
+//       orders through their final rows, Q_m'[k, J':] g_m'[J':]                      | barrier
+//   X2  (one CTA per signal, float64)  the recurrence over m' = hi .. lo through the tracked rows,
+//       Q_m'[k, :J'] g_m'[:J'], in shared memory; the final entries written back into the bins;
+//       column scales of every g_m of the block                                      | barrier
+//   Y   (tensor cores)  F_m = P_m^{-1} g_m for every order of the block (Eq. (14)); f_l^{+-m},
+//       column scales of F_m                                                          | barrier
+//   Z   (tensor cores)  G_{+-m'}(theta_k) = P~_m'(theta_k) F_m' for every order of the block and
+//       ring k < m' (Eq. (16))                                                        | barrier
+//   E   (all CTAs)  G subtracted from bins alias_k(+-m') of every ring (Eq. (15)) that a later
+//       block reads (the block's own rows are final and are skipped)                  | barrier
+//
+// Five grid barriers per block (the last block stops after Y): 5 L / kChainB in all, where one
+// phase per order needs three per order.  Y and Z items are (order, 128 x 64 tile) with the whole
+// K range, so each item converts its exact int64 accumulators to float64 and stores the result
+// itself.  The right-hand sides are read in float64 and cut into BF16 slices while staged in shared
 // memory, with the column scales the previous phase gathered; the plan tables (P_m^{-1}, P~) are
-// pre-sliced.
+// pre-sliced and loaded by TMA.
 //
 // The cooperative launch guarantees that every CTA is resident, so the barriers cannot wait on a
-// CTA that never runs.  Every wait is bounded (one second); a CTA that gives up sets the plan's
-// status word and an abort word that every other CTA checks in its barrier waits, so all of them
-// leave the chain promptly and release their tensor memory.  Data written by other SMs in an
-// earlier phase is read through L2 (cp.async.cg, __ldcg), never through a possibly stale L1 line.
+// CTA that never runs.  Every wait is bounded (the plan's wait limit); a CTA that gives up sets the
+// plan's status word and an abort word that every other CTA checks in its barrier waits, so all of
+// them leave the chain promptly and release their tensor memory.  Data written by other SMs in an
+// earlier phase is read through L2 (cp.async.cg, __ldcg, TMA), never through a possibly stale L1
+// line.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -43,81 +53,28 @@ namespace {
 // columns 0..31 and 32..63 of the tile, so each thread accumulates 32 int64 values.
 constexpr int kThreads = 256;
 constexpr int kCols = NT / 2;
+constexpr int kB = kChainB;
 
 struct ChainArgs {
-    int L, Nc;                       // Nc = 4 * batch columns
+    int L, Nc, B;                    // Nc = 4 B columns
     double *W, *F;                   // order-major bins and solved orders (rows_total x Nc)
     double2 *coeffs;
-    const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // P_m^{-1} slices
-    const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;   // P~ slices
-    long long *part_s, *part_a;      // K-split partials of the solves and of the alias products,
-                                     // int64 at the scale of the output element (2^-(eA + eB)
-                                     // 2^shift): splits x M x Nc
-    unsigned *bar;                   // [0] arrivals (monotonic within a launch), [64] abort:
-                                     // separate 128-byte lines
-    int *eW, *eF;                    // [2][Nc] largest exponent fields of the columns of g_m
-                                     // without its first row, and of F_m (slot m & 1)
-    int *fS;                         // [Nc] fields of g_m's columns, first row included
-                                     // (all of bar, eW, eF, fS zeroed per launch)
+    const int *piE, *ptE;            // row scale exponents of the P_m^{-1} and P~ slices
+    const double *Q;                 // Q_m = P~_m(rings lo..m-1) P_m^{-1}: kB x n_m at kB rows_off(L, m)
+    double *H;                       // tracked entries of the current block: rows x Nc
+    double *G;                       // Z's output: block order i at i L Nc, row k (ring), Nc columns
+    int *eW, *eF;                    // L x Nc exponent fields of the columns of g_m and of F_m
+    unsigned *bar;                   // [0] arrivals (monotonic within a launch), [64] abort
     uint64_t wait_ns;                // limit of every wait on other CTAs or on the pipeline
     const unsigned char *tmaps;      // TMA maps of the table slices: order m at 2m (P_m^{-1}) and
                                      // 2m + 1 (P~ block), kTensorMapBytes each
     int *status;
 };
 
-// Exact int64 sum of K-split partials, then one conversion: 2^(eA_r + eB_c - shift) * sum.
-struct Scales {
-    const int *eA;     // row scale exponents
-    const int *fB;     // exponent fields of the right-hand side's columns
-    int shift;
-};
-struct Partials {
-    const long long *part;
-    int M, splits;
-    Scales sc;
-};
-
-// First row of a solve's right-hand side g_m: ring m, whose bins +-m still hold order m+1's
-// alias contribution; `a` is the bin alias_m(m + 1) it was aliased into.
-struct FirstRow {
-    bool pending;      // m + 1 < L
-    Partials alias;    // order m+1's alias partials (row m of them is ring m)
-    int a;
-};
-
-// One contraction C (M x Nc) = A (M x K, plan slices) B (K x Nc, float64, row-major).
-struct Job {
-    const void *tmap; const int *eA; int kp;   // A: TMA map {kp, rows, slices}, row scales
-    const double *B; const int *eB;  // eB: exponent fields of B's columns (the solve: without the
-                                     // first row, which the items complete with `first`)
-    long long *part;                 // destination of the partials
-    const FirstRow *first;           // solves: completion of the first row (null: alias products)
-    int M, K, tiles_n, tiles, splits, kchunk;
-};
-
-__device__ __forceinline__ int cdiv_i(int a, int b) { return (a + b - 1) / b; }
-
-__device__ Job make_job(const void *tmap, const int *eA, int kp, const double *B, const int *eB, int M,
-                        int K, int Nc) {
-    Job j;
-    j.tmap = tmap; j.eA = eA; j.kp = kp; j.B = B; j.eB = eB; j.M = M; j.K = K;
-    j.part = nullptr; j.first = nullptr;
-    j.tiles_n = cdiv_i(Nc, NT);
-    j.tiles = cdiv_i(M, MT) * j.tiles_n;
-    j.splits = 1;
-    j.kchunk = K;
-    const int G = (int)gridDim.x;
-    if (j.tiles < G) {
-        // one round of items over the grid: K-splits of whole 32-row blocks
-        int sp = min(min(G / j.tiles, cdiv_i(K, KB)), kSplitCap);
-        if (sp > 1) {
-            const int kc = cdiv_i(cdiv_i(K, sp), KB) * KB;
-            sp = cdiv_i(K, kc);
-            if (sp > 1) { j.splits = sp; j.kchunk = kc; }
-        }
-    }
-    return j;
-}
+// Block geometry.  Block b covers orders hi = L-1-b kB down to lo = max(0, hi-kB+1); its order
+// m = hi - i has J(i) = floor((i+1)/2) tracked rows (rings m .. m+J-1), stored from row offH(i) of H.
+__host__ __device__ __forceinline__ int blk_J(int i) { return (i + 1) >> 1; }
+__host__ __device__ __forceinline__ int blk_offH(int i) { const int p = i >> 1; return p * p + (i & 1) * p; }
 
 __device__ __forceinline__ bool aborted(const ChainArgs &p) {
     return *(volatile unsigned *)(p.bar + 64) != 0u;
@@ -153,120 +110,110 @@ __device__ bool grid_barrier(const ChainArgs &p, int *s_flag, unsigned &target) 
     return *s_flag != 0;
 }
 
-// Largest exponent field of each column over `rows` rows of the row-major block X (Nc columns)
-// into ef[Nc] (atomicMax).  CTA c takes rows c, c + G, ..; each thread keeps the maximum of its
-// column over eight rows in flight at a time, so each column sees at most G atomics.
-__device__ void column_fields(const ChainArgs &p, const double *X, int rows, int *ef) {
-    const int Nc = p.Nc, C = (int)gridDim.x;
-    for (int j = threadIdx.x; j < Nc; j += kThreads) {
-        int mf = 0;
-        for (int r0 = blockIdx.x; r0 < rows; r0 += 8 * C) {
-            double x[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int r = r0 + u * C;
-                x[u] = r < rows ? __ldcg(X + (int64_t)r * Nc + j) : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) mf = max(mf, exp_field(x[u]));
-        }
-        if (mf > 0) atomicMax(ef + j, mf);
+// Subtract the contributions (G+ = g[0..1] re/im, G- = g[2..3] re/im) of an order m' from the four
+// columns of one signal in row (o, ring k) of the bins, where a = alias_k(m') is the bin of G+
+// (o = |a|): bin a gets G+, bin -a gets G-; slot 0 holds bin +o, slot 2 bin -o (zero for o = 0).
+__device__ __forceinline__ void sub_alias(double w[4], int a, const double g[4]) {
+    if (a == 0) {
+        w[0] -= g[0] + g[2];
+        w[1] -= g[1] + g[3];
+    } else if (a > 0) {
+        w[0] -= g[0]; w[1] -= g[1]; w[2] -= g[2]; w[3] -= g[3];
+    } else {
+        w[0] -= g[2]; w[1] -= g[3]; w[2] -= g[0]; w[3] -= g[1];
     }
 }
 
-// Exact int64 sum of the K-split partials of row r, columns c0..c0+3 (all at the scale of the
-// output element), then one conversion: 2^(eA_r + eB_c - shift) * sum.
-__device__ __forceinline__ void sum_partials(const ChainArgs &p, const Partials &pa, int r, int c0, double v[4]) {
-    const int Nc = p.Nc, M = pa.M, splits = pa.splits;
-    long long t[4] = {0, 0, 0, 0};
-    for (int y0 = 0; y0 < splits; y0 += 8) {
-        longlong2 a[8], b[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (y0 + u < splits) {
-                const longlong2 *pp = reinterpret_cast<const longlong2 *>(pa.part + ((int64_t)(y0 + u) * M + r) * Nc + c0);
-                a[u] = __ldcg(pp);
-                b[u] = __ldcg(pp + 1);
-            }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-            if (y0 + u < splits) { t[0] += a[u].x; t[1] += a[u].y; t[2] += b[u].x; t[3] += b[u].y; }
+// The same contributions as they land in the row's four columns (what sub_alias subtracts).
+__device__ __forceinline__ void alias_map(int a, const double g[4], double out[4]) {
+    if (a == 0) {
+        out[0] = g[0] + g[2]; out[1] = g[1] + g[3]; out[2] = 0.0; out[3] = 0.0;
+    } else if (a > 0) {
+        out[0] = g[0]; out[1] = g[1]; out[2] = g[2]; out[3] = g[3];
+    } else {
+        out[0] = g[2]; out[1] = g[3]; out[2] = g[0]; out[3] = g[1];
     }
-    const int er = pa.sc.eA[r] - pa.sc.shift;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = i64_scaled(t[q], er + scale_from_field(__ldcg(pa.sc.fB + c0 + q)));
 }
 
-// The contraction's items (output tile, K-split), one per CTA and round; each stores its int64
-// partial.  `ok` turns false (for the whole CTA) when an mbarrier wait gives up.
-// NSL BF16 slices per operand (kind::f16), or, with TF, one TF32 value per operand (kind::tf32:
-// the table rows pre-scaled and rounded at plan time, the right-hand side scaled by its column
-// scale and rounded here), accumulated in FP32 as the single-region low-precision path.
+// One contraction of a phase: C (M x Nc) = A (M x K, plan slices) B (K x Nc, float64, row-major).
+struct Job {
+    const void *tmap; const int *eA; int kp;   // A: TMA map {kp, rows, slices}, row scales
+    const double *B; const int *eB;            // eB: exponent fields of B's columns
+    int M, K, tiles_n, tiles;
+    int mode;                                  // 0: solve (Y), 1: alias values (Z)
+    int m;                                     // the order
+    double *out;                               // Y: F block m; Z: G rows of the order
+    int *ef;                                   // Y: exponent fields of F_m's columns
+};
+
+__device__ __forceinline__ int cdiv_i(int a, int b) { return (a + b - 1) / b; }
+
+// Job of block order i (m = hi - i) in phase Y (solve) or Z (alias).
+__device__ Job make_job(const ChainArgs &p, bool solve, int hi, int i) {
+    const int L = p.L, Nc = p.Nc, m = hi - i, n = L - m;
+    Job j;
+    j.tiles_n = cdiv_i(Nc, NT);
+    j.m = m;
+    j.K = n;
+    j.kp = (n + 7) & ~7;
+    if (solve) {
+        j.tmap = p.tmaps + (size_t)(2 * m) * kTensorMapBytes;
+        j.eA = p.piE + rows_off(L, m);
+        j.B = p.W + rows_off(L, m) * Nc;
+        j.eB = p.eW + (int64_t)m * Nc;
+        j.M = n;
+        j.mode = 0;
+        j.out = p.F + rows_off(L, m) * Nc;
+        j.ef = p.eF + (int64_t)m * Nc;
+    } else {
+        j.tmap = p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes;
+        j.eA = p.ptE + (int64_t)m * L;
+        j.B = p.F + rows_off(L, m) * Nc;
+        j.eB = p.eF + (int64_t)m * Nc;
+        j.M = m;   // rings 0 .. m-1
+        j.mode = 1;
+        j.out = p.G + (int64_t)i * L * Nc;
+        j.ef = nullptr;
+    }
+    j.tiles = j.M > 0 ? cdiv_i(j.M, MT) * j.tiles_n : 0;
+    return j;
+}
+
+// The items (block order, output tile) of phase Y or Z, one per CTA and round, each over the whole
+// K range; each stores its float64 result.  `ok` turns false (for the whole CTA) when an mbarrier
+// wait gives up.  NSL BF16 slices per operand (kind::f16), or, with TF, one TF32 value per operand
+// (kind::tf32: the table rows pre-scaled and rounded at plan time, the right-hand side scaled by its
+// column scale and rounded here), accumulated in FP32 as the single-region low-precision path.
 template <int NSL, bool TF>
-__device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32_t tbase,
+__device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, int lo, uint32_t tbase,
                                        unsigned char *smem, uint64_t *mbar, uint64_t *full,
                                        uint32_t uses[2], uint32_t fills[2], bool &ok) {
     constexpr bool EXACT = NSL == S && !TF;
     constexpr int NREG = EXACT ? REGIONS : 1;
-    const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2;
-    const int Nc = p.Nc, M = jb.M;
-    const int items = jb.tiles * jb.splits;
-    __shared__ int s_eb[NT];        // scale exponents of the tile's B columns
-    __shared__ double s_row0[NT];   // solve: the tile's part of g_m's first row
-    __shared__ double s_v[NT];      // solve: order m+1's alias sums for that row
+    constexpr int SHIFT = EXACT ? ACC_SHIFT : 40;
+    const int tid = threadIdx.x, warp = tid >> 5, half = warp >> 2, lane = tid & 31;
+    const int Nc = p.Nc, nb = hi - lo + 1;
+    __shared__ int s_eb[NT];           // scale exponents of the tile's B columns
+    __shared__ int s_start[kB + 1];    // first item of each block order
+    __syncthreads();
+    if (tid == 0) {
+        s_start[0] = 0;
+        for (int i = 0; i < nb; ++i) s_start[i + 1] = s_start[i] + make_job(p, solve, hi, i).tiles;
+    }
+    __syncthreads();
+    const int items = s_start[nb];
     for (int it = blockIdx.x; it < items && ok; it += gridDim.x) {
-        const int tile = it / jb.splits, y = it - tile * jb.splits;
+        int i = 0;
+        while (s_start[i + 1] <= it) ++i;
+        const Job jb = make_job(p, solve, hi, i);
+        const int tile = it - s_start[i];
         const int tm = tile / jb.tiles_n, tn = tile - tm * jb.tiles_n;
         const int row0 = tm * MT, col0 = tn * NT;
-        const int kbeg = y * jb.kchunk, kend = min(jb.K, kbeg + jb.kchunk);
+        const int kend = jb.K;
         __syncthreads();   // the previous item's epilogue is done with s_eb
-        if (jb.first) {
-            // ring m of the tile's 16 signals with order m+1's alias contribution removed (every
-            // item of a column computes the same values, hence the same column scale): one thread
-            // per column sums the alias partials exactly, then applies the bin mapping of EPI_ALIAS
-            const FirstRow &fr = *jb.first;
-            const int col = col0 + tid;
-            if (tid < NT) {
-                double v = 0.0;
-                if (fr.pending && col < Nc) {
-                    const Partials &pa = fr.alias;
-                    const int r = pa.M - 1;
-                    long long t = 0;
-                    for (int y0 = 0; y0 < pa.splits; y0 += 8) {
-                        long long a8[8];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u)
-                            a8[u] = y0 + u < pa.splits ? __ldcg(pa.part + ((int64_t)(y0 + u) * pa.M + r) * Nc + col) : 0ll;
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) t += a8[u];
-                    }
-                    v = i64_scaled(t, pa.sc.eA[r] - pa.sc.shift + scale_from_field(__ldcg(pa.sc.fB + col)));
-                }
-                s_v[tid] = v;
-            }
-            __syncthreads();
-            if (tid < NT) {
-                double w = col < Nc ? __ldcg(jb.B + col) : 0.0;
-                if (fr.pending && col < Nc) {
-                    const int q = tid & 3, b0 = tid & ~3;
-                    if (fr.a == 0) {
-                        if (q < 2) w -= s_v[b0 + q] + s_v[b0 + q + 2];
-                    } else {
-                        const int sp = fr.a > 0 ? 0 : 2;   // slot of bin a: receives G_{+}
-                        w -= (q >> 1) == (sp >> 1) ? s_v[b0 + (q & 1)] : s_v[b0 + 2 + (q & 1)];
-                    }
-                }
-                s_row0[tid] = w;
-            }
-            __syncthreads();
-        }
         if (tid < NT) {
             const int col = col0 + tid;
-            int f = col < Nc ? __ldcg(jb.eB + col) : 0;
-            if (jb.first && col < Nc) {
-                f = max(f, exp_field(s_row0[tid]));
-                if (tm == 0 && y == 0) p.fS[col] = f;
-            }
+            const int f = col < Nc ? __ldcg(jb.eB + col) : 0;
             s_eb[tid] = scale_from_field(f);
         }
         __syncthreads();
@@ -293,11 +240,10 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
             const int e = s_eb[j];
             double x[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int k = kbase + 2 * (h + 4 * (i >> 1)) + (i & 1);
-                x[i] = (col < Nc && k < kend) ? __ldcg(jb.B + (int64_t)k * Nc + col) : 0.0;
+            for (int q = 0; q < 8; ++q) {
+                const int k = kbase + 2 * (h + 4 * (q >> 1)) + (q & 1);
+                x[q] = (col < Nc && k < kend) ? __ldcg(jb.B + (int64_t)k * Nc + col) : 0.0;
             }
-            if (jb.first && kbase == 0 && h == 0) x[0] = s_row0[j];   // row 0: g_m's completed first row
             const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
             if (TF) {
                 // canonical K-major layout of 32-bit elements: core matrices of 8 columns x 4 K
@@ -315,15 +261,15 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int kk = 2 * (h + 4 * q);
-                __nv_bfloat16 lo[S], hi[S];
-                split_value(x[2 * q], e, lo);
-                split_value(x[2 * q + 1], e, hi);
+                __nv_bfloat16 lo_s[S], hi_s[S];
+                split_value(x[2 * q], e, lo_s);
+                split_value(x[2 * q + 1], e, hi_s);
                 const uint32_t a = cb + (kk >> 3) * (NT * 16) + (kk & 7) * 2;
 #pragma unroll
                 for (int s = 0; s < NSL; ++s)
                     asm volatile("st.shared.u32 [%0], %1;\n" ::"r"(a + s * (NT * KB * 2)),
-                                 "r"((uint32_t)__bfloat16_as_ushort(lo[s]) |
-                                     ((uint32_t)__bfloat16_as_ushort(hi[s]) << 16))
+                                 "r"((uint32_t)__bfloat16_as_ushort(lo_s[s]) |
+                                     ((uint32_t)__bfloat16_as_ushort(hi_s[s]) << 16))
                                  : "memory");
             }
         };
@@ -331,12 +277,12 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
         long long acc[kCols];   // columns half * kCols .. of row quarter * 32 + lane
 #pragma unroll
         for (int c = 0; c < kCols; ++c) acc[c] = 0;
-        const int kb0 = kbeg / KB, nkb = (kend + KB - 1) / KB;
-        load(kb0, 0);
+        const int nkb = (kend + KB - 1) / KB;
+        load(0, 0);
         fence_proxy_async();
         __syncthreads();
-        for (int kb = kb0; kb < nkb; ++kb) {
-            const int st = (kb - kb0) & 1;
+        for (int kb = 0; kb < nkb; ++kb) {
+            const int st = kb & 1;
             // stage st holds k-block kb once its TMA load has landed: issue its MMAs, then stage the
             // next block while they run
             {
@@ -355,12 +301,12 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                         if (kg >= kend) break;
                         const uint64_t ad = sdesc_sw64(sa + (q >> 1) * TF_A_HALF + 32 * (q & 1));
                         const uint64_t bd = sdesc(sb + 2 * q * (NT * 16), NT * 16, 128);
-                        mma_tf32(tbase, ad, bd, kIdescTf32, kg == kbeg ? 0u : 1u);
+                        mma_tf32(tbase, ad, bd, kIdescTf32, kg == 0 ? 0u : 1u);
                     }
                 for (int hh = 0; hh < 2 && !TF; ++hh) {
                     const int kg = kb * KB + 16 * hh;
                     if (kg >= kend) break;
-                    if (kg == kbeg || (EXACT && kg % CHUNK == 0))
+                    if (kg == 0 || (EXACT && kg % CHUNK == 0))
                         for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
                     for (int s = 1; s <= NSL; ++s)
                         for (int t = 1; s + t <= NSL + 1; ++t) {
@@ -405,18 +351,18 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
                             float v[16];
                             tmem_ld16(lane_base + reg * NT + c0, v);
 #pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                acc[c0 + i] += (long long)__float2int_rn(v[i] * up) << shift;
+                            for (int q = 0; q < 16; ++q)
+                                acc[c0 + q] += (long long)__float2int_rn(v[q] * up) << shift;
                         }
                     }
                 } else {
-                    // one rounded FP32 sum over the whole K-split: kept at 2^-40 resolution
+                    // one rounded FP32 sum over the whole K range: kept at 2^-40 resolution
 #pragma unroll
                     for (int c0 = 0; c0 < kCols; c0 += 16) {
                         float v[16];
                         tmem_ld16(lane_base + c0, v);
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) acc[c0 + i] = __float2ll_rn(v[i] * 0x1p40f);
+                        for (int q = 0; q < 16; ++q) acc[c0 + q] = __float2ll_rn(v[q] * 0x1p40f);
                     }
                 }
                 tc_fence_before();
@@ -425,73 +371,182 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, const Job &jb, uint32
         }
         if (!ok) break;
 
-        const int row = row0 + (warp & 3) * 32 + (tid & 31);
-        if (row < M) {
+        // epilogue: one conversion per element, 2^(eA_row + eB_col - SHIFT) * acc
+        const int row = row0 + (warp & 3) * 32 + lane;
+        const bool live = row < jb.M;
+        const int er = live ? __ldg(jb.eA + row) - SHIFT : 0;
+        double v[kCols];
+#pragma unroll
+        for (int c = 0; c < kCols; ++c) v[c] = live ? i64_scaled(acc[c], er + s_eb[half * kCols + c]) : 0.0;
+        if (jb.mode == 0) {
+            const EpiArgs es{jb.out, Nc, nullptr, jb.m, p.L, Nc, p.coeffs, nullptr};
 #pragma unroll
             for (int g = 0; g < kCols / 4; ++g) {
-                const int cl = half * kCols + 4 * g, c0 = col0 + cl;
-                if (c0 >= Nc) break;
-                long long *pp = jb.part + ((int64_t)y * M + row) * Nc + c0;
-                *reinterpret_cast<longlong2 *>(pp) = make_longlong2(acc[4 * g], acc[4 * g + 1]);
-                *reinterpret_cast<longlong2 *>(pp + 2) = make_longlong2(acc[4 * g + 2], acc[4 * g + 3]);
+                const int c0 = col0 + half * kCols + 4 * g;
+                if (live && c0 < Nc) epilogue_row4<EPI_SOLVE>(es, row, c0, v + 4 * g);
             }
+            // largest exponent field of each column over the tile's rows: warp maximum, one
+            // atomic per warp and column
+#pragma unroll
+            for (int c = 0; c < kCols; ++c) {
+                const unsigned f = __reduce_max_sync(0xffffffffu, (unsigned)exp_field(v[c]));
+                const int col = col0 + half * kCols + c;
+                if (lane == 0 && f > 0u && col < Nc) atomicMax(jb.ef + col, (int)f);
+            }
+        } else if (live) {
+            double *o = jb.out + (int64_t)row * Nc + col0 + half * kCols;
+#pragma unroll
+            for (int c = 0; c < kCols; c += 2)
+                if (col0 + half * kCols + c < Nc) *reinterpret_cast<double2 *>(o + c) = make_double2(v[c], v[c + 1]);
         }
     }
 }
 
-// The reduction phase of order m:
-//  (a) the solve's partials -> F_m rows and f_l^{+-m}; largest exponent fields of F_m's columns
-//      into ef (gathered per CTA in shared memory when the grid's thread count is a multiple of
-//      the column groups: every thread then stays on one group and the CTA's groups are a window
-//      of kThreads groups; one global atomicMax per CTA and column);
-//  (b) order m+1's alias sums subtracted from the bins of rings k < m (ring m, the first row of
-//      g_m, was completed by the solve's items and is not needed again);
-//  (c) largest exponent fields of g_{m-1}'s columns over its rows 1.. (rings >= m: final, and
-//      untouched by (b)) into efw.
-__device__ __noinline__ void reduce_phase(const ChainArgs &p, const EpiArgs &es, const Partials &ps, int *ef,
-                                          bool prev, const EpiArgs &ea, const Partials &pa,
-                                          const double *gnext, int gnext_rows, int *efw) {
-    const int groups = p.Nc / 4;
-    const int64_t T = (int64_t)gridDim.x * kThreads;
-    {
-        const int64_t total = (int64_t)ps.M * groups;
-        __shared__ int s_ef[4 * kThreads];
-        const bool windowed = T % groups == 0;
-        const int g0 = (int)(((int64_t)blockIdx.x * kThreads) % groups);
-        const int span = min(groups, kThreads);
-        for (int i = threadIdx.x; i < 4 * kThreads; i += kThreads) s_ef[i] = 0;
-        __syncthreads();
-        for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
-            const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
-            double v[4];
-            sum_partials(p, ps, r, 4 * g, v);
-            epilogue_row4<EPI_SOLVE>(es, r, 4 * g, v);
-            const int w = g - g0 < 0 ? g - g0 + groups : g - g0;   // position in the CTA's window
+// X1: the tracked entries of block [lo, hi], signal s: row (m, j) (ring k = m + j) of the bins less
+// the contributions of the block's orders m' that reach it, through their rows J'.. (final),
+// Q_m'[k, J':] g_m'[J':].  One warp per (entry, signal), lanes along the row; into H.
+__device__ void phase_x1(const ChainArgs &p, int hi, int lo) {
+    const int L = p.L, Nc = p.Nc, B = p.B, nE = blk_offH(hi - lo + 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t w = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; w < (int64_t)nE * B; w += nw) {
+        const int e = (int)(w / B), s = (int)(w - (int64_t)e * B);
+        int i = 0;
+        while (blk_offH(i + 1) <= e) ++i;
+        const int m = hi - i, j = e - blk_offH(i), k = m + j;
+        double acc[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int mp = hi; mp > k; --mp) {
+            const int a = alias_bin(mp, k);
+            if ((a < 0 ? -a : a) != m) continue;
+            const int Jp = blk_J(hi - mp), np = L - mp;
+            const double *q = p.Q + (int64_t)kB * rows_off(L, mp) + (int64_t)(k - lo) * np;
+            const double *g = p.W + rows_off(L, mp) * Nc + 4 * s;
+            double gs[4] = {0.0, 0.0, 0.0, 0.0};
+            for (int c = Jp + lane; c < np; c += 32) {
+                const double qv = __ldg(q + c);
+                const double2 g01 = __ldcg(reinterpret_cast<const double2 *>(g + (int64_t)c * Nc));
+                const double2 g23 = __ldcg(reinterpret_cast<const double2 *>(g + (int64_t)c * Nc + 2));
+                gs[0] = fma(qv, g01.x, gs[0]);
+                gs[1] = fma(qv, g01.y, gs[1]);
+                gs[2] = fma(qv, g23.x, gs[2]);
+                gs[3] = fma(qv, g23.y, gs[3]);
+            }
+            double mapped[4];
+            alias_map(a, gs, mapped);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int f = exp_field(v[q]);
-                if (f == 0) continue;
-                if (windowed) atomicMax(&s_ef[4 * w + q], f);
-                else atomicMax(ef + 4 * g + q, f);
-            }
+            for (int q4 = 0; q4 < 4; ++q4) acc[q4] += mapped[q4];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) acc[q4] += __shfl_xor_sync(0xffffffffu, acc[q4], o);
+        if (lane < 4) {
+            const double wv = __ldcg(p.W + (rows_off(L, m) + j) * Nc + 4 * s + lane);
+            p.H[(int64_t)e * Nc + 4 * s + lane] = wv - acc[lane];
+        }
+    }
+}
+
+// X2: per signal (one CTA each), the recurrence of the tracked entries over the block's orders
+// m' = hi .. lo: once every order above m' is applied, rows 0..J'-1 of g_m' are final, and its
+// contribution Q_m'[k, :J'] g_m'[:J'] is subtracted from the tracked entries it reaches (rings
+// lo <= k < m').  The entries and Q's leading columns live in shared memory.  Then the final
+// entries go back into the bins, the exponent fields of every g_m of the block (all its rows) are
+// gathered for Y, and F_m's fields are cleared for Y's atomics.
+__device__ void phase_x2(const ChainArgs &p, int hi, int lo, double *sm) {
+    const int L = p.L, Nc = p.Nc, nb = hi - lo + 1, nE = blk_offH(nb), tid = threadIdx.x;
+    __shared__ int s_qoff[kB + 1];    // order i's Q block: (m - lo) rings x J(i) columns
+    __shared__ int s_f[kB * 4];       // exponent fields of the block's g_m, four columns
+    if ((int)blockIdx.x < p.B) {
+        if (tid == 0) {
+            s_qoff[0] = 0;
+            for (int i = 0; i < nb; ++i) s_qoff[i + 1] = s_qoff[i] + (hi - i - lo) * blk_J(i);
         }
         __syncthreads();
-        if (windowed)
-            for (int i = threadIdx.x; i < 4 * span; i += kThreads) {
-                const int w = i >> 2, g = g0 + w < groups ? g0 + w : g0 + w - groups;
-                if (s_ef[i] > 0) atomicMax(ef + 4 * g + (i & 3), s_ef[i]);
+        double *qs = sm, *hs = sm + s_qoff[nb];
+        for (int t = tid; t < s_qoff[nb]; t += kThreads) {
+            int i = 0;
+            while (s_qoff[i + 1] <= t) ++i;
+            const int J = blk_J(i), r = t - s_qoff[i], kk = r / J, c = r - kk * J, m = hi - i;
+            qs[t] = __ldg(p.Q + (int64_t)kB * rows_off(L, m) + (int64_t)kk * (L - m) + c);
+        }
+        for (int s = blockIdx.x; s < p.B; s += gridDim.x) {
+            __syncthreads();
+            for (int t = tid; t < 4 * nE; t += kThreads) hs[t] = __ldcg(p.H + (int64_t)(t >> 2) * Nc + 4 * s + (t & 3));
+            for (int t = tid; t < 4 * nb; t += kThreads) s_f[t] = 0;
+            __syncthreads();
+            for (int ip = 0; ip < nb; ++ip) {
+                const int mp = hi - ip, Jp = blk_J(ip);
+                if (Jp > 0) {
+                    const double *h = hs + 4 * blk_offH(ip);      // rows 0..Jp-1 of g_m' (final)
+                    for (int t = tid; t < 4 * (mp - lo); t += kThreads) {
+                        const int kk = t >> 2, q4 = t & 3, k = lo + kk;
+                        const int a = alias_bin(mp, k), o = a < 0 ? -a : a;
+                        if (o < lo || k - o >= blk_J(hi - o)) continue;   // not a tracked entry
+                        if (a == 0 && q4 >= 2) continue;                 // bin 0: slots 2, 3 stay zero
+                        const int c1 = a >= 0 ? q4 : (q4 ^ 2);            // source column (alias_map)
+                        const double *qr = qs + s_qoff[ip] + kk * Jp;
+                        double g = 0.0;
+                        for (int c = 0; c < Jp; ++c) {
+                            const double hv = a == 0 ? h[4 * c + q4] + h[4 * c + q4 + 2] : h[4 * c + c1];
+                            g = fma(qr[c], hv, g);
+                        }
+                        hs[4 * (blk_offH(hi - o) + (k - o)) + q4] -= g;
+                    }
+                }
+                __syncthreads();
             }
-    }
-    if (prev) {
-        const int64_t total = (int64_t)(pa.M - 1) * groups;
-        for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < total; t += T) {
-            const int r = (int)(t / groups), g = (int)(t - (int64_t)r * groups);
-            double v[4];
-            sum_partials(p, pa, r, 4 * g, v);
-            epilogue_row4<EPI_ALIAS>(ea, r, 4 * g, v);
+            // the final entries back into the bins
+            for (int t = tid; t < 4 * nE; t += kThreads) {
+                const int e = t >> 2;
+                int i = 0;
+                while (blk_offH(i + 1) <= e) ++i;
+                const int m = hi - i, j = e - blk_offH(i);
+                p.W[(rows_off(L, m) + j) * Nc + 4 * s + (t & 3)] = hs[t];
+            }
+            __syncthreads();
+            // exponent fields of the columns of g_m (every row), for the slicing in Y
+            for (int i = 0; i < nb; ++i) {
+                const int m = hi - i, n = L - m;
+                const double *g = p.W + rows_off(L, m) * Nc + 4 * s;
+                int f = 0;
+                for (int r = tid >> 2; r < n; r += kThreads >> 2) f = max(f, exp_field(__ldcg(g + (int64_t)r * Nc + (tid & 3))));
+                if (f > 0) atomicMax(&s_f[4 * i + (tid & 3)], f);
+            }
+            __syncthreads();
+            for (int t = tid; t < 4 * nb; t += kThreads) {
+                const int m = hi - (t >> 2);
+                p.eW[(int64_t)m * Nc + 4 * s + (t & 3)] = s_f[t];
+                p.eF[(int64_t)m * Nc + 4 * s + (t & 3)] = 0;
+            }
         }
     }
-    if (gnext) column_fields(p, gnext, gnext_rows, efw);
+    // the shared buffer is the MMA stages' next: order these generic accesses before the TMA writes
+    fence_proxy_async();
+}
+
+// E: the block's alias values subtracted from the bins that a later block reads.  Thread = (ring k,
+// signal), orders m' = hi .. max(lo, k+1) in turn (several may reach the same bin: fixed order).
+__device__ void phase_e(const ChainArgs &p, int hi, int lo) {
+    const int L = p.L, Nc = p.Nc, B = p.B;
+    const int64_t T = (int64_t)gridDim.x * kThreads;
+    for (int64_t t = (int64_t)blockIdx.x * kThreads + threadIdx.x; t < (int64_t)hi * B; t += T) {
+        const int k = (int)(t / B), s = (int)(t - (int64_t)k * B);
+        for (int mp = hi; mp >= lo && mp > k; --mp) {
+            const int a = alias_bin(mp, k), o = a < 0 ? -a : a;
+            if (o >= lo) continue;   // a row of the block's own orders: final, not read again
+            const double *gp = p.G + ((int64_t)(hi - mp) * L + k) * Nc + 4 * s;
+            const double2 g01 = __ldcg(reinterpret_cast<const double2 *>(gp));
+            const double2 g23 = __ldcg(reinterpret_cast<const double2 *>(gp + 2));
+            const double g[4] = {g01.x, g01.y, g23.x, g23.y};
+            double2 *wp = reinterpret_cast<double2 *>(p.W + (rows_off(L, o) + (k - o)) * Nc + 4 * s);
+            const double2 w01 = __ldcg(wp), w23 = __ldcg(wp + 1);
+            double w[4] = {w01.x, w01.y, w23.x, w23.y};
+            sub_alias(w, a, g);
+            wp[0] = make_double2(w[0], w[1]);
+            wp[1] = make_double2(w[2], w[3]);
+        }
+    }
 }
 
 template <int NSL, bool TF>
@@ -518,55 +573,22 @@ __global__ void __launch_bounds__(kThreads, 1) k_chain(ChainArgs p) {
 
     uint32_t uses[2] = {0u, 0u}, fills[2] = {0u, 0u};
     unsigned target = 0;   // arrivals that complete the next grid barrier
-    bool ok = true, mma_ok = true;
-    const int L = p.L, Nc = p.Nc;
-    constexpr int SHIFT = NSL == S && !TF ? ACC_SHIFT : 40;
-    for (int m = L - 1; m >= 0; --m) {
-        const int n = L - m, kp = (n + 7) & ~7, sl = m & 1;
-        // order m+1's alias products: their partials are still in part_a
-        FirstRow first;
-        first.pending = m + 1 < L;
-        first.a = 0;
-        first.alias = Partials{p.part_a, 0, 0, Scales{nullptr, nullptr, SHIFT}};
-        if (first.pending) {
-            const int n1 = n - 1;
-            const Job jp = make_job(nullptr, nullptr, (n1 + 7) & ~7, nullptr, nullptr, m + 1, n1, Nc);
-            first.alias = Partials{p.part_a, m + 1, jp.splits,
-                                   Scales{p.ptE + (int64_t)(m + 1) * L, p.eF + (sl ^ 1) * Nc, SHIFT}};
-            first.a = alias_bin(m + 1, m);
-        }
-        // Eq. (14): F_m = P_m^{-1} g_m
-        Job js = make_job(p.tmaps + (size_t)(2 * m) * kTensorMapBytes, p.piE + rows_off(L, m), kp,
-                          p.W + rows_off(L, m) * Nc, p.eW + sl * Nc, n, n, Nc);
-        js.part = p.part_s;
-        js.first = &first;
-        mma_phase<NSL, TF>(p, js, tbase, smem, mbar, full, uses, fills, mma_ok);
-        if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
-        if (!(ok = grid_barrier(p, &s_flag, target))) break;
-        {
-            const EpiArgs es{p.F + rows_off(L, m) * Nc, Nc, nullptr, m, L, Nc, p.coeffs, nullptr};
-            const Partials ps{p.part_s, n, js.splits, Scales{js.eA, p.fS, SHIFT}};
-            const EpiArgs ea{nullptr, Nc, nullptr, m + 1, L, Nc, nullptr, p.W};
-            const double *gn = m >= 1 ? p.W + (rows_off(L, m - 1) + 1) * Nc : nullptr;
-            reduce_phase(p, es, ps, p.eF + sl * Nc, first.pending, ea, first.alias, gn, L - m,
-                         p.eW + (sl ^ 1) * Nc);
-        }
-        if (!(ok = grid_barrier(p, &s_flag, target))) break;
-        if (m == 0) break;
-        // slots read for the last time: eW of order m, eF of order m + 1 (next written by the
-        // reductions of orders m - 1 and m - 1)
-        for (int j = blockIdx.x * kThreads + tid; j < Nc; j += gridDim.x * kThreads) {
-            p.eW[sl * Nc + j] = 0;
-            p.eF[(sl ^ 1) * Nc + j] = 0;
-        }
-        // Eqs. (15)-(16): orders +-m out of the bins of rings k < m (partials only; summed and
-        // subtracted in the next order's phases)
-        Job ja = make_job(p.tmaps + (size_t)(2 * m + 1) * kTensorMapBytes, p.ptE + (int64_t)m * L, kp,
-                          p.F + rows_off(L, m) * Nc, p.eF + sl * Nc, m, n, Nc);
-        ja.part = p.part_a;
-        mma_phase<NSL, TF>(p, ja, tbase, smem, mbar, full, uses, fills, mma_ok);
-        if (!mma_ok) { if (tid == 0) raise_abort(p, 1); ok = false; break; }
-        if (!(ok = grid_barrier(p, &s_flag, target))) break;
+    bool mma_ok = true;
+    for (int hi = p.L - 1; hi >= 0; hi -= kB) {
+        const int lo = max(0, hi - kB + 1);
+        phase_x1(p, hi, lo);
+        if (!grid_barrier(p, &s_flag, target)) break;
+        phase_x2(p, hi, lo, reinterpret_cast<double *>(smem));
+        if (!grid_barrier(p, &s_flag, target)) break;
+        mma_phase<NSL, TF>(p, true, hi, lo, tbase, smem, mbar, full, uses, fills, mma_ok);
+        if (!mma_ok) { if (tid == 0) raise_abort(p, 1); break; }
+        if (!grid_barrier(p, &s_flag, target)) break;
+        if (lo == 0) break;   // no order below: the chain is done
+        mma_phase<NSL, TF>(p, false, hi, lo, tbase, smem, mbar, full, uses, fills, mma_ok);
+        if (!mma_ok) { if (tid == 0) raise_abort(p, 1); break; }
+        if (!grid_barrier(p, &s_flag, target)) break;
+        phase_e(p, hi, lo);
+        if (!grid_barrier(p, &s_flag, target)) break;
     }
     if (!mma_ok) {
         // let the TMA loads and MMAs in flight finish (bounded) before the CTA releases its
@@ -594,6 +616,24 @@ cudaError_t launch_chain(const ChainArgs &p, int grid, cudaStream_t s) {
     cfg.attrs = at;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_chain<NSL, TF>, p);
+}
+
+// Q_m = P~_m(rings lo..m-1) P_m^{-1} for every order m (lo the first order of m's block): CTA
+// (m, y) takes rings lo + y, lo + y + gridDim.y, ..; thread = column c of Q (coalesced reads of
+// P_m^{-1}'s rows), float64.
+__global__ void k_chain_q(int L, const double *__restrict__ pt, const double *__restrict__ pinv, double *__restrict__ Q) {
+    const int m = blockIdx.x, n = L - m;
+    const int hi = L - 1 - ((L - 1 - m) / kB) * kB, lo = max(0, hi - kB + 1);
+    const double *pi = pinv + pinv_off(L, m);
+    double *q = Q + (int64_t)kB * rows_off(L, m);
+    for (int r = blockIdx.y; r < m - lo; r += gridDim.y) {
+        const double *prow = pt + pt_off(L, m) + (int64_t)(lo + r) * n;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            double acc = 0.0;
+            for (int l = 0; l < n; ++l) acc = fma(__ldg(prow + l), __ldg(pi + (int64_t)l * n + c), acc);
+            q[(int64_t)r * n + c] = acc;
+        }
+    }
 }
 
 }  // namespace
@@ -645,7 +685,13 @@ cudaError_t tc_table_tensor_maps_tf32(int L, const float *piT, const std::vector
     return cudaMemcpy(*d_maps, maps.data(), bytes, cudaMemcpyHostToDevice);
 }
 
-int64_t tc_chain_words(int64_t batch) { return kChainBarWords + 5 * 4 * batch; }
+int64_t tc_chain_words(int L, int64_t batch) { return kChainBarWords + 2 * (int64_t)L * 4 * batch; }
+
+cudaError_t tc_chain_q_table(int L, const double *pt, const double *pinv, double *Q, cudaStream_t s) {
+    if (L <= 1) return cudaSuccess;
+    k_chain_q<<<dim3((unsigned)L, (unsigned)std::min(L, kB)), 128, 0, s>>>(L, pt, pinv, Q);
+    return cudaGetLastError();
+}
 
 cudaError_t tc_prepare_chain(int *grid) {
     cudaError_t e;
@@ -665,20 +711,19 @@ cudaError_t tc_prepare_chain(int *grid) {
 }
 
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, double *part, double *part2, unsigned *words, int *status,
+                             double2 *coeffs, double *H, double *G, unsigned *words, int *status,
                              int nsl, bool tf32, int grid, uint64_t wait_ns, cudaStream_t s) {
     ChainArgs p{};
-    p.L = L; p.Nc = (int)(4 * batch);
+    p.L = L; p.B = (int)batch; p.Nc = (int)(4 * batch);
     p.W = W; p.F = F; p.coeffs = coeffs;
-    p.piS = t.piS; p.piE = t.piE; p.pik_off = t.pik_off;
-    p.ptS = t.ptS; p.ptE = t.ptE; p.ptk_off = t.ptk_off;
+    p.piE = t.piE; p.ptE = t.ptE; p.Q = t.Q;
     p.tmaps = t.tmaps;
-    p.part_s = reinterpret_cast<long long *>(part); p.part_a = reinterpret_cast<long long *>(part2);
+    p.H = H; p.G = G;
     p.bar = words; p.status = status; p.wait_ns = wait_ns;
     p.eW = reinterpret_cast<int *>(words + kChainBarWords);
-    p.eF = p.eW + 2 * p.Nc;
-    p.fS = p.eF + 2 * p.Nc;
-    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * tc_chain_words(batch), s);
+    p.eF = p.eW + (int64_t)L * p.Nc;
+    // the barrier words only: the kernel writes every field it reads before reading it
+    cudaError_t e = cudaMemsetAsync(words, 0, sizeof(unsigned) * kChainBarWords, s);
     if (e != cudaSuccess) return e;
     if (tf32) return launch_chain<1, true>(p, grid, s);
     if (nsl == S) return launch_chain<S, false>(p, grid, s);

@@ -104,7 +104,7 @@ struct Workspace {
     int *xE = nullptr;
     unsigned char *tmX = nullptr;    // tensor plans: TMA maps of the X slices
     unsigned *bar = nullptr;         // tensor plans: words of the chain kernel (tc_chain_words)
-    double *part2 = nullptr;         // tensor plans: the chain's alias partials (as `part`)
+    double *part2 = nullptr;         // tensor plans: the chain's alias values, kChainB * L * 4B
     double2 *r = nullptr, *dx = nullptr;  // refinement: residual, update
     uint64_t bytes = 0;
 };
@@ -147,6 +147,7 @@ struct sht_plan_s {
     // their TMA maps, read by the low-precision chain
     float *ptT = nullptr, *piT = nullptr;
     unsigned char *d_tmaps_tf32 = nullptr;
+    double *chainQ = nullptr;           // tensor plans: tc_chain_q_table
     bool refine_tf32 = false;
     std::vector<int64_t> ptk_off, pik_off;
     int *d_status = nullptr;
@@ -329,7 +330,15 @@ struct ChainTables {
     const __nv_bfloat16 *piS; const int *piE; const int64_t *pik_off;   // device offsets
     const __nv_bfloat16 *ptS; const int *ptE; const int64_t *ptk_off;
     const unsigned char *tmaps;   // device: 2 L TMA maps (tc_table_tensor_maps)
+    const double *Q;              // device: tc_chain_q_table
 };
+// The chain kernel takes the orders in blocks of kChainB (L-1 down): block b covers orders
+// hi = L-1-b kChainB .. lo = max(0, hi-kChainB+1).
+constexpr int kChainB = 32;
+// Q_m = P~_m(theta_k) P_m^{-1} for the rings lo <= k < m of m's block (float64, from the plan's pt
+// and pinv): order m at kChainB * rows_off(L, m), (m - lo) rows of n_m, row k - lo.  The chain's
+// tracked entries follow from it (the alias contribution of order m at ring k is Q_m[k] g_m).
+cudaError_t tc_chain_q_table(int L, const double *pt, const double *pinv, double *Q, cudaStream_t s);
 constexpr int kTensorMapBytes = 128;
 // TMA maps of the sliced tables for the chain kernel, order m at 2m (P_m^{-1} block: {kp, n, S})
 // and 2m + 1 (P~ block: {kp, L, S}), boxes of 32 x 128 x S, 64-byte swizzle; written to a new
@@ -343,11 +352,13 @@ cudaError_t tc_table_tensor_maps_tf32(int L, const float *piT, const std::vector
                                       unsigned char **d_maps);
 constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 128-byte lines
 cudaError_t tc_prepare_chain(int *grid);
+// H: kSplitCap L Nc doubles of scratch (the tracked entries); G: kChainB L Nc doubles (a block's
+// alias values); words: tc_chain_words(L, batch) (barrier, exponent fields).
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, double *part, double *part2, unsigned *words, int *status,
+                             double2 *coeffs, double *H, double *G, unsigned *words, int *status,
                              int nsl, bool tf32, int grid, uint64_t wait_ns, cudaStream_t s);
 // Device words the chain kernel needs beside W, F and part (barrier, column scales).
-int64_t tc_chain_words(int64_t batch);
+int64_t tc_chain_words(int L, int64_t batch);
 // TMA maps of the per-call X slices (order m at m: {kp, 4B, S}, boxes 32 x 64 x S), written to a
 // new device array *d_maps of L * kTensorMapBytes bytes (the caller frees it).
 cudaError_t tc_x_tensor_maps(int L, int64_t batch, const __nv_bfloat16 *xS,

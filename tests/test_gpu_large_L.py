@@ -86,7 +86,7 @@ def test_L512_elementwise_against_oracle(dtype, recipe):
     p.close()
 
 
-@pytest.mark.parametrize("L", [1024])
+@pytest.mark.parametrize("L", [1024, 2048])
 @pytest.mark.parametrize("dtype", ["f64", "f64_tensor"])
 def test_full_size_against_stored_oracle_values(L, dtype):
     from paper_1403_4661_gb300.sht import Plan
