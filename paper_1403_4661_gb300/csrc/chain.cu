@@ -292,8 +292,7 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
             if (tid == 0) {
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
-                bool fresh[REGIONS] = {false, false, false, false, false, false};
-                if (TF)
+                if (TF) {
                     for (int q = 0; q < 4; ++q) {
                         // K = 8 per MMA: 32 bytes along a 64-byte swizzled A row, two core
                         // matrices of B
@@ -303,19 +302,14 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
                         const uint64_t bd = sdesc(sb + 2 * q * (NT * 16), NT * 16, 128);
                         mma_tf32(tbase, ad, bd, kIdescTf32, kg == 0 ? 0u : 1u);
                     }
-                for (int hh = 0; hh < 2 && !TF; ++hh) {
-                    const int kg = kb * KB + 16 * hh;
-                    if (kg >= kend) break;
-                    if (kg == 0 || (EXACT && kg % CHUNK == 0))
-                        for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
-                    for (int s = 1; s <= NSL; ++s)
-                        for (int t = 1; s + t <= NSL + 1; ++t) {
-                            const int d = s + t, reg = EXACT ? (d <= 6 ? d - 2 : 5) : 0;
-                            const uint64_t ad = sdesc_sw64(sa + (s - 1) * (MT * KB * 2) + 32 * hh);
-                            const uint64_t bd = sdesc(sb + (t - 1) * (NT * KB * 2) + 2 * hh * (NT * 16), NT * 16, 128);
-                            mma_bf16(tbase + reg * NT, ad, bd, kIdesc, fresh[reg] ? 0u : 1u);
-                            fresh[reg] = false;
-                        }
+                } else {
+                    // two 16-K steps; the first of a chunk (or of the item) restarts the regions
+                    constexpr uint32_t A16 = (MT * KB * 2) >> 4, B16 = (NT * KB * 2) >> 4;
+                    const uint64_t ad0 = sdesc_sw64(sa), bd0 = sdesc(sb, NT * 16, 128);
+                    const bool restart = kb == 0 || (EXACT && (kb * KB) % CHUNK == 0);
+                    mma_slice_pairs<NSL, EXACT, A16, B16>(tbase, ad0, bd0, restart);
+                    if (kb * KB + 16 < kend)
+                        mma_slice_pairs<NSL, EXACT, A16, B16>(tbase, ad0 + (32 >> 4), bd0 + ((2 * NT * 16) >> 4), false);
                 }
                 mma_commit(smem_u32(&mbar[st]));
             }

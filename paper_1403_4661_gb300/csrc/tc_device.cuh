@@ -160,6 +160,29 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                             ((uint32_t)(MT >> 4) << 24);
+// The slice-pair MMAs of one 16-K step: A slice s (1..NSL) times B slice t with s + t <= NSL + 1 (the
+// pairs of weight 2^-7(s+t) down to the float64 unit).  With EXACT, diagonal d = s + t accumulates in
+// TMEM region d - 2 (d <= 6: exact in FP32 over a CHUNK) or 5 (d >= 7: the rounded tail), otherwise
+// every pair in region 0.  Fully unrolled: each pair's region and whether it is its region's first
+// MMA of the step are compile-time constants, and the shared-memory descriptors advance from ad0 /
+// bd0 by constant offsets in 16-byte units (A_SLICE16, B_SLICE16 per slice; the addresses stay below
+// 2^18, so the 14-bit address field never carries).  `restart`: the first MMA of every region
+// overwrites its accumulator instead of adding to it.
+template <int NSL, bool EXACT, uint32_t A_SLICE16, uint32_t B_SLICE16>
+__device__ __forceinline__ void mma_slice_pairs(uint32_t tbase, uint64_t ad0, uint64_t bd0, bool restart) {
+#pragma unroll
+    for (int s = 1; s <= NSL; ++s) {
+#pragma unroll
+        for (int t = 1; t <= NSL + 1 - s; ++t) {
+            const int d = s + t;
+            const int reg = EXACT ? (d <= 6 ? d - 2 : 5) : 0;
+            const bool lead = s == 1 && (EXACT ? d <= 7 : t == 1);
+            mma_bf16(tbase + reg * NT, ad0 + (uint64_t)((s - 1) * A_SLICE16), bd0 + (uint64_t)((t - 1) * B_SLICE16),
+                     kIdesc, (lead && restart) ? 0u : 1u);
+        }
+    }
+}
+
 // Instruction descriptor, kind::tf32: D = F32, A = B = TF32 (format code 2), both K-major.
 constexpr uint32_t kIdescTf32 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                 ((uint32_t)(MT >> 4) << 24);

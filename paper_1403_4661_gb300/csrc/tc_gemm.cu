@@ -190,21 +190,11 @@ __global__ void __launch_bounds__(kSynThreads, 1) k_synthesis(SynArgs p) {
             if (ok0) {
                 tc_fence_after();
                 const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
-                bool fresh[REGIONS] = {false, false, false, false, false, false};
-                for (int hh = 0; hh < 2; ++hh) {
-                    const int kg = kb * KB + 16 * hh;
-                    if (kg >= K) break;
-                    if (kg % CHUNK == 0)
-                        for (int r = 0; r < REGIONS; ++r) fresh[r] = true;
-                    for (int s = 1; s <= S; ++s)
-                        for (int t = 1; s + t <= S + 1; ++t) {
-                            const int d = s + t, reg = d <= 6 ? d - 2 : 5;
-                            const uint64_t ad = sdesc_sw64(sa + (s - 1) * (MT * KB * 2) + 32 * hh);
-                            const uint64_t bd = sdesc_sw64(sb + (t - 1) * (NT * KB * 2) + 32 * hh);
-                            mma_bf16(tbase + reg * NT, ad, bd, kIdesc, fresh[reg] ? 0u : 1u);
-                            fresh[reg] = false;
-                        }
-                }
+                // two 16-K steps; the first of a chunk restarts the accumulator regions
+                constexpr uint32_t A16 = (MT * KB * 2) >> 4, B16 = (NT * KB * 2) >> 4;
+                const uint64_t ad0 = sdesc_sw64(sa), bd0 = sdesc_sw64(sb);
+                mma_slice_pairs<S, true, A16, B16>(tbase, ad0, bd0, (kb * KB) % CHUNK == 0);
+                if (kb * KB + 16 < K) mma_slice_pairs<S, true, A16, B16>(tbase, ad0 + (32 >> 4), bd0 + (32 >> 4), false);
                 mma_commit(smem_u32(&mbar[st]));
                 ++commits;
                 // refill the other stage once the MMAs of block kb - 1 (its last reader) are done
