@@ -550,9 +550,10 @@ constexpr int kBarWords = 96;   // arrival counter [0], abort word [32], small-s
 constexpr int kMaxTeam = 16;    // CTAs of one team chain: two team barriers per order each
 
 // Forward phase 2's schedule.  The chain of a signal of band-limit L costs ~L^3; a signal whose
-// chain exceeds half a CTA's fair share of the batch (share = sum of L^3 over the grid) runs on a
-// team of T = min(16, ceil(2 L^3 / share)) CTAs (L >= 64), so that no task is much above half a
-// share and list scheduling stays within ~1.5 shares; the others run on one CTA each from a queue.
+// chain exceeds two CTAs' fair share of the batch (share = sum of L^3 over the grid) runs on a
+// team of T = min(16, floor(L^3 / share)) CTAs (L >= 64); the others run on one CTA each from a
+// queue.  (Splitting every chain above half a share, into ceil(2 L^3 / share) members, measured
+// slower on the 512-signal workload: more teams leave more CTAs waiting for team partners.)
 // Teams, largest first, take consecutive CTAs, wrapping to CTA 0 when the grid is used up; every
 // CTA runs its team tasks in the order they were dealt, so a team waits only for members busy
 // with earlier teams.
@@ -566,7 +567,7 @@ void plan_teams(const std::vector<USig> &hs, const std::vector<int> &lpt, int gr
     nteams = 0;
     for (int i : lpt) {
         const double w = (double)hs[(size_t)i].L * hs[(size_t)i].L * hs[(size_t)i].L;
-        int T = hs[(size_t)i].L >= 64 ? (int)std::min<double>(kMaxTeam, std::ceil(2.0 * w / share)) : 1;
+        int T = hs[(size_t)i].L >= 64 ? (int)std::min<double>(kMaxTeam, std::floor(w / share)) : 1;
         T = std::min(T, grid);
         if (T < 2) { small.push_back(i); continue; }
         if (cursor + T > grid) cursor = 0;
