@@ -513,7 +513,7 @@ cudaError_t forward_impl(sht_plan_t p, Workspace &w, const double2 *d_samples, d
         const ChainTables t{p->piS, p->piE, p->d_pik_off, p->ptS, p->ptE, p->d_ptk_off,
                             tf32 ? p->d_tmaps_tf32 : p->d_tmaps, p->chainQ};
         if (e == cudaSuccess)
-            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part, w.part2, w.bar, p->d_status, nsl,
+            e = tc_forward_chain(t, L, batch, W, F, d_coeffs, w.part2, w.bar, p->d_status, nsl,
                                  tf32, p->chain_grid, p->wait_ns, s);
         p->launches += 1;
         return e;

@@ -11,11 +11,12 @@
 // Q_m'[k] g_m' with Q_m' = P~_m' P_m'^{-1} (plan table, rings lo <= k < m'), the tracked entries
 // follow from a small recurrence, and the block's heavy products run all at once.  Per block:
 //
-//   X1  (all CTAs, float64)  tracked entries: ring bins less the contributions of the block's
-//       orders through their final rows, Q_m'[k, J':] g_m'[J':]                      | barrier
-//   X2  (one CTA per signal, float64)  the recurrence over m' = hi .. lo through the tracked rows,
-//       Q_m'[k, :J'] g_m'[:J'], in shared memory; the final entries written back into the bins;
-//       column scales of every g_m of the block                                      | barrier
+//   X1  (all CTAs, float64)  the contributions of the block's orders to the tracked entries
+//       through their final rows, Q_m'[k, J':] g_m'[J':]                             | barrier
+//   X2  (one CTA per signal, float64)  the tracked entries (bins less those contributions), then
+//       the recurrence over m' = hi .. lo through the tracked rows, Q_m'[k, :J'] g_m'[:J'], in
+//       shared memory; the final entries written back into the bins; column scales of every g_m
+//       of the block                                                                 | barrier
 //   Y   (tensor cores)  F_m = P_m^{-1} g_m for every order of the block (Eq. (14)); f_l^{+-m},
 //       column scales of F_m                                                          | barrier
 //   Z   (tensor cores)  G_{+-m'}(theta_k) = P~_m'(theta_k) F_m' for every order of the block and
@@ -61,8 +62,8 @@ struct ChainArgs {
     double2 *coeffs;
     const int *piE, *ptE;            // row scale exponents of the P_m^{-1} and P~ slices
     const double *Q;                 // Q_m = P~_m(rings lo..m-1) P_m^{-1}: kB x n_m at kB rows_off(L, m)
-    double *H;                       // tracked entries of the current block: rows x Nc
-    double *G;                       // Z's output: block order i at i L Nc, row k (ring), Nc columns
+    double *G;                       // Z's output: block order i at i L Nc, row k (ring), Nc columns;
+                                     // X1's output (before Z): row (hi - m') kB + (k - lo)
     int *eW, *eF;                    // L x Nc exponent fields of the columns of g_m and of F_m
     unsigned *bar;                   // [0] arrivals (monotonic within a launch), [64] abort
     uint64_t wait_ns;                // limit of every wait on other CTAs or on the pipeline
@@ -221,7 +222,17 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
         // k-block kb into stage st: the A slices (all S of them, 128 rows x 32 K, 64-byte
         // swizzled; zero beyond the table) by one TMA load; B read in float64 (rows >= kend as
         // zero) and sliced here, thread = column j, row pairs (2i, 2i + 1), i = h, h + 4, ..
-        auto load = [&](int kb, int st) {
+        // B values of a k-block (thread = column j, rows 2(h + 4i) + {0, 1}), fetched one k-block
+        // ahead of their slicing so that the loads' latency hides behind a whole iteration
+        auto fetch = [&](int kb, double x[8]) {
+            const int j = tid & (NT - 1), h = tid >> 6, col = col0 + j, kbase = kb * KB;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int k = kbase + 2 * (h + 4 * (q >> 1)) + (q & 1);
+                x[q] = (col < Nc && k < kend) ? __ldcg(jb.B + (int64_t)k * Nc + col) : 0.0;
+            }
+        };
+        auto load = [&](int kb, int st, const double *x) {
             const uint32_t sa = smem_u32(smem + st * STAGE), sb = sa + A_STAGE;
             const int kbase = kb * KB;
             if (tid == 0) {
@@ -236,14 +247,8 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
                 }
             }
             fills[st] += 1;
-            const int j = tid & (NT - 1), h = tid >> 6, col = col0 + j;
+            const int j = tid & (NT - 1), h = tid >> 6;
             const int e = s_eb[j];
-            double x[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int k = kbase + 2 * (h + 4 * (q >> 1)) + (q & 1);
-                x[q] = (col < Nc && k < kend) ? __ldcg(jb.B + (int64_t)k * Nc + col) : 0.0;
-            }
             const uint32_t cb = sb + (j >> 3) * 128 + (j & 7) * 16;
             if (TF) {
                 // canonical K-major layout of 32-bit elements: core matrices of 8 columns x 4 K
@@ -278,7 +283,10 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
 #pragma unroll
         for (int c = 0; c < kCols; ++c) acc[c] = 0;
         const int nkb = (kend + KB - 1) / KB;
-        load(0, 0);
+        double xn[8];   // the next k-block's B values
+        fetch(0, xn);
+        load(0, 0, xn);
+        if (nkb > 1) fetch(1, xn);
         fence_proxy_async();
         __syncthreads();
         for (int kb = 0; kb < nkb; ++kb) {
@@ -320,7 +328,11 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
                 const int ns = st ^ 1;
                 const bool w = uses[ns] == 0 || mbar_wait(smem_u32(&mbar[ns]), (uses[ns] - 1) & 1u, p.wait_ns);
                 if (!__syncthreads_and(w)) { ok = false; break; }
-                load(kb + 1, ns);
+                double xc[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) xc[q] = xn[q];
+                if (kb + 2 < nkb) fetch(kb + 2, xn);
+                load(kb + 1, ns, xc);
                 fence_proxy_async();
                 __syncthreads();
             }
@@ -396,48 +408,40 @@ __device__ __noinline__ void mma_phase(const ChainArgs &p, bool solve, int hi, i
     }
 }
 
-// X1: the tracked entries of block [lo, hi], signal s: row (m, j) (ring k = m + j) of the bins less
-// the contributions of the block's orders m' that reach it, through their rows J'.. (final),
-// Q_m'[k, J':] g_m'[J':].  One warp per (entry, signal), lanes along the row; into H.
+// X1: for every order m' of block [lo, hi] and ring k (lo <= k < m') whose alias bin is a tracked
+// entry, the contribution of m' through its final rows, Q_m'[k, J':] g_m'[J':] (the four columns
+// G+ re/im, G- re/im of each signal), into the scratch rows (hi - m') kB + (k - lo) of p.G.  One
+// warp per (order, ring, signal), lanes along the row, so that every warp does one row's work
+// whatever the number of orders that reach an entry (X2 adds them up per entry).
 __device__ void phase_x1(const ChainArgs &p, int hi, int lo) {
-    const int L = p.L, Nc = p.Nc, B = p.B, nE = blk_offH(hi - lo + 1);
+    const int L = p.L, Nc = p.Nc, B = p.B, nb = hi - lo + 1;
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
-    for (int64_t w = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; w < (int64_t)nE * B; w += nw) {
-        const int e = (int)(w / B), s = (int)(w - (int64_t)e * B);
-        int i = 0;
-        while (blk_offH(i + 1) <= e) ++i;
-        const int m = hi - i, j = e - blk_offH(i), k = m + j;
-        double acc[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int mp = hi; mp > k; --mp) {
-            const int a = alias_bin(mp, k);
-            if ((a < 0 ? -a : a) != m) continue;
-            const int Jp = blk_J(hi - mp), np = L - mp;
-            const double *q = p.Q + (int64_t)kB * rows_off(L, mp) + (int64_t)(k - lo) * np;
-            const double *g = p.W + rows_off(L, mp) * Nc + 4 * s;
-            double gs[4] = {0.0, 0.0, 0.0, 0.0};
-            for (int c = Jp + lane; c < np; c += 32) {
-                const double qv = __ldg(q + c);
-                const double2 g01 = __ldcg(reinterpret_cast<const double2 *>(g + (int64_t)c * Nc));
-                const double2 g23 = __ldcg(reinterpret_cast<const double2 *>(g + (int64_t)c * Nc + 2));
-                gs[0] = fma(qv, g01.x, gs[0]);
-                gs[1] = fma(qv, g01.y, gs[1]);
-                gs[2] = fma(qv, g23.x, gs[2]);
-                gs[3] = fma(qv, g23.y, gs[3]);
-            }
-            double mapped[4];
-            alias_map(a, gs, mapped);
-#pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) acc[q4] += mapped[q4];
+    const int64_t total = (int64_t)nb * kB * B;
+    for (int64_t w = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5; w < total; w += nw) {
+        const int pr = (int)(w / B), s = (int)(w - (int64_t)pr * B);
+        const int ip = pr / kB, kk = pr - ip * kB, mp = hi - ip, k = lo + kk;
+        if (k >= mp) continue;                                   // rings below m' only
+        const int a = alias_bin(mp, k), o = a < 0 ? -a : a;
+        if (o < lo || k - o >= blk_J(hi - o)) continue;          // not a tracked entry
+        const int Jp = blk_J(ip), np = L - mp;
+        const double *q = p.Q + (int64_t)kB * rows_off(L, mp) + (int64_t)kk * np;
+        const double *g = p.W + rows_off(L, mp) * Nc + 4 * s;
+        double gs[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int c = Jp + lane; c < np; c += 32) {
+            const double qv = __ldg(q + c);
+            const double2 g01 = __ldcg(reinterpret_cast<const double2 *>(g + (int64_t)c * Nc));
+            const double2 g23 = __ldcg(reinterpret_cast<const double2 *>(g + (int64_t)c * Nc + 2));
+            gs[0] = fma(qv, g01.x, gs[0]);
+            gs[1] = fma(qv, g01.y, gs[1]);
+            gs[2] = fma(qv, g23.x, gs[2]);
+            gs[3] = fma(qv, g23.y, gs[3]);
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
+        for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) acc[q4] += __shfl_xor_sync(0xffffffffu, acc[q4], o);
-        if (lane < 4) {
-            const double wv = __ldcg(p.W + (rows_off(L, m) + j) * Nc + 4 * s + lane);
-            p.H[(int64_t)e * Nc + 4 * s + lane] = wv - acc[lane];
-        }
+            for (int q4 = 0; q4 < 4; ++q4) gs[q4] += __shfl_xor_sync(0xffffffffu, gs[q4], off);
+        if (lane < 4) p.G[(int64_t)pr * Nc + 4 * s + lane] = gs[lane];
     }
 }
 
@@ -466,7 +470,22 @@ __device__ void phase_x2(const ChainArgs &p, int hi, int lo, double *sm) {
         }
         for (int s = blockIdx.x; s < p.B; s += gridDim.x) {
             __syncthreads();
-            for (int t = tid; t < 4 * nE; t += kThreads) hs[t] = __ldcg(p.H + (int64_t)(t >> 2) * Nc + 4 * s + (t & 3));
+            // tracked entries: the bins less X1's contributions of the orders that reach them
+            for (int t = tid; t < 4 * nE; t += kThreads) {
+                const int e = t >> 2, q4 = t & 3;
+                int i = 0;
+                while (blk_offH(i + 1) <= e) ++i;
+                const int m = hi - i, j = e - blk_offH(i), k = m + j;
+                double v = __ldcg(p.W + (rows_off(L, m) + j) * Nc + 4 * s + q4);
+                for (int mp = hi; mp > k; --mp) {
+                    const int a = alias_bin(mp, k);
+                    if ((a < 0 ? -a : a) != m) continue;
+                    if (a == 0 && q4 >= 2) continue;              // bin 0: slots 2, 3 stay zero
+                    const double *gp = p.G + ((int64_t)(hi - mp) * kB + (k - lo)) * Nc + 4 * s;
+                    v -= a == 0 ? __ldcg(gp + q4) + __ldcg(gp + q4 + 2) : __ldcg(gp + (a > 0 ? q4 : (q4 ^ 2)));
+                }
+                hs[t] = v;
+            }
             for (int t = tid; t < 4 * nb; t += kThreads) s_f[t] = 0;
             __syncthreads();
             for (int ip = 0; ip < nb; ++ip) {
@@ -705,14 +724,14 @@ cudaError_t tc_prepare_chain(int *grid) {
 }
 
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, double *H, double *G, unsigned *words, int *status,
+                             double2 *coeffs, double *G, unsigned *words, int *status,
                              int nsl, bool tf32, int grid, uint64_t wait_ns, cudaStream_t s) {
     ChainArgs p{};
     p.L = L; p.B = (int)batch; p.Nc = (int)(4 * batch);
     p.W = W; p.F = F; p.coeffs = coeffs;
     p.piE = t.piE; p.ptE = t.ptE; p.Q = t.Q;
     p.tmaps = t.tmaps;
-    p.H = H; p.G = G;
+    p.G = G;
     p.bar = words; p.status = status; p.wait_ns = wait_ns;
     p.eW = reinterpret_cast<int *>(words + kChainBarWords);
     p.eF = p.eW + (int64_t)L * p.Nc;

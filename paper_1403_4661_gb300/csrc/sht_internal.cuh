@@ -352,10 +352,10 @@ cudaError_t tc_table_tensor_maps_tf32(int L, const float *piT, const std::vector
                                       unsigned char **d_maps);
 constexpr int kChainBarWords = 96;   // grid barrier of the chain kernel: three 128-byte lines
 cudaError_t tc_prepare_chain(int *grid);
-// H: kSplitCap L Nc doubles of scratch (the tracked entries); G: kChainB L Nc doubles (a block's
-// alias values); words: tc_chain_words(L, batch) (barrier, exponent fields).
+// G: kChainB L Nc doubles of scratch (a block's alias values, and the look-ahead's contributions);
+// words: tc_chain_words(L, batch) (barrier, exponent fields).
 cudaError_t tc_forward_chain(const ChainTables &t, int L, int64_t batch, double *W, double *F,
-                             double2 *coeffs, double *H, double *G, unsigned *words, int *status,
+                             double2 *coeffs, double *G, unsigned *words, int *status,
                              int nsl, bool tf32, int grid, uint64_t wait_ns, cudaStream_t s);
 // Device words the chain kernel needs beside W, F and part (barrier, column scales).
 int64_t tc_chain_words(int L, int64_t batch);
