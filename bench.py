@@ -234,6 +234,35 @@ def _config(args):
             "launch": "one CUDA graph per step" if not getattr(args, "no_graph", False) else "eager"}
 
 
+def _vs_stored_oracle(L, seed, s, c2):
+    """Signal 0 of the batch against the oracle at the seeded indices stored for it in
+    tests/golden/oracle_L{L}.txt (written from oracle/ only, for this same signal: decaying spectrum,
+    seed 1000, the stored greedy rings): the GPU inverse against the oracle's inverse, and the GPU
+    round trip forward(inverse(c)) against the oracle's.  None when there is no record for L."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_L{L}.txt")
+    if seed != 1000 or not os.path.exists(path):
+        return None
+    hdr, ci, cv, si, sv = {}, [], [], [], []
+    for line in open(path):
+        if line.startswith("#"):
+            continue
+        f = line.split()
+        if f[0] == "c":
+            ci.append(int(f[1])); cv.append(float(f[2]) + 1j * float(f[3]))
+        elif f[0] == "s":
+            si.append(int(f[1])); sv.append(float(f[2]) + 1j * float(f[3]))
+        else:
+            hdr[f[0]] = f[1]
+    if int(hdr.get("seed", -1)) != seed:
+        return None
+    c_g = c2[0].cpu().numpy()[np.array(ci)]
+    s_g = s[0].cpu().numpy()[np.array(si)]
+    return {"coeff_max_abs_diff": float(np.abs(c_g - np.array(cv)).max()),
+            "sample_max_rel_diff": float(np.abs(s_g - np.array(sv)).max() / max(1.0, float(hdr["max_abs_s"]))),
+            "n_coeff": len(ci), "n_sample": len(si), "oracle_E1_max": float(hdr["oracle_E1_max"]),
+            "source": f"tests/golden/oracle_L{L}.txt"}
+
+
 def run_ours(args):
     import torch
 
@@ -294,6 +323,7 @@ def run_ours(args):
         eager_step()
     torch.cuda.synchronize()
     err = (c2 - c).abs().max().item()
+    vs_oracle = _vs_stored_oracle(L, 1000 + rank, s, c2) if args.dtype != "f32" else None
     step = eager_step
     graph = None
     if not args.no_graph:
@@ -422,7 +452,8 @@ def run_ours(args):
         "config": dict(_config(args), parallelism=f"dp{ws}" if ws > 1 else "single GPU"),
         "accuracy": {"E1_max_round_trip": err, "E1_max_round_trip_e2e": err_e2e,
                      "definition": "max |forward(inverse(c)) - c| over the batch, both GPU transforms "
-                                   "(Exp. 1 of Sec. IV-A); GPU-vs-oracle parity is checked by the tests"},
+                                   "(Exp. 1 of Sec. IV-A); GPU-vs-oracle parity is checked by the tests",
+                     "vs_oracle_sampled": vs_oracle},
         "roofline": roof,
         "forms": forms,
         "cpu_baseline": cpu,

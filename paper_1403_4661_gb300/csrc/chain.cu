@@ -477,12 +477,16 @@ __device__ void phase_x2(const ChainArgs &p, int hi, int lo, double *sm) {
                 while (blk_offH(i + 1) <= e) ++i;
                 const int m = hi - i, j = e - blk_offH(i), k = m + j;
                 double v = __ldcg(p.W + (rows_off(L, m) + j) * Nc + 4 * s + q4);
+                // every order above ring k: its scratch row exists, so the loads carry no branch
+                // and several are in flight; orders that do not reach this entry add nothing
+#pragma unroll 4
                 for (int mp = hi; mp > k; --mp) {
                     const int a = alias_bin(mp, k);
-                    if ((a < 0 ? -a : a) != m) continue;
-                    if (a == 0 && q4 >= 2) continue;              // bin 0: slots 2, 3 stay zero
+                    const bool hit = (a < 0 ? -a : a) == m && !(a == 0 && q4 >= 2);   // bin 0: slots 2, 3 stay zero
                     const double *gp = p.G + ((int64_t)(hi - mp) * kB + (k - lo)) * Nc + 4 * s;
-                    v -= a == 0 ? __ldcg(gp + q4) + __ldcg(gp + q4 + 2) : __ldcg(gp + (a > 0 ? q4 : (q4 ^ 2)));
+                    const double g1 = __ldcg(gp + (a >= 0 ? q4 : (q4 ^ 2)));
+                    const double g2 = a == 0 ? __ldcg(gp + (q4 & 1) + 2) : 0.0;
+                    v -= hit ? g1 + g2 : 0.0;
                 }
                 hs[t] = v;
             }
