@@ -1,5 +1,5 @@
-"""Structured O(n^2) per-order solve (Sec. IV-C's complexity discussion): the study behind the
-structured-solve section of the design notes, kept as a CPU test.
+"""Structured O(n^2) per-order solve (Sec. IV-C's complexity discussion), a study kept as a CPU
+test: the library's plans keep explicit inverses, and this checks the O(n^2) alternative.
 
 P_m[k][j] = P~_{m+j}^m(theta_k) satisfies the three-term recursion of Sec. III-G along j, so
 diag(cos theta) P_m - P_m T = u e_{n-1}^T with T the symmetric tridiagonal recursion (Jacobi) matrix:
