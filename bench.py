@@ -205,6 +205,8 @@ def run_reference(args):
                        "then forward SHT by the oracle's Procedures 2 and 1 (plain float64, host CPU); "
                        "timed on a bounded sample, see cpu_baseline.sample")
     cfg["launch"] = "host processes, one per core"
+    cfg["l2"] = "host memory; no GPU is used"
+    cfg["e2e"] = "the oracle reads and writes host arrays: no copies, e2e equals the value"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "signals/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
