@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "fft_device.cuh"
+#include "uneven_schedule.h"
 
 namespace sht {
 namespace {
@@ -55,11 +56,6 @@ struct USig {
     int64_t off;      // complex-element offset of the signal in the caller's arrays
     int64_t ws;       // double offset of the signal's scratch (4 columns per row)
     int64_t item0;    // first item of the signal in the per-(signal, order / ring) phases
-};
-
-// One member's share of a team chain: signal, rank in the team, team size, team index.
-struct UTask {
-    int sig, rank, T, team;
 };
 
 struct UArgs {
@@ -547,40 +543,6 @@ void uneven_free(sht_uneven_t u) {
 }
 
 constexpr int kBarWords = 96;   // arrival counter [0], abort word [32], small-signal queue [64]
-constexpr int kMaxTeam = 16;    // CTAs of one team chain: two team barriers per order each
-
-// Forward phase 2's schedule.  The chain of a signal of band-limit L costs ~L^3; a signal whose
-// chain exceeds two CTAs' fair share of the batch (share = sum of L^3 over the grid) runs on a
-// team of T = min(16, floor(L^3 / share)) CTAs (L >= 64); the others run on one CTA each from a
-// queue.  (Splitting every chain above half a share, into ceil(2 L^3 / share) members, measured
-// slower on the 512-signal workload: more teams leave more CTAs waiting for team partners.)
-// Teams, largest first, take consecutive CTAs, wrapping to CTA 0 when the grid is used up; every
-// CTA runs its team tasks in the order they were dealt, so a team waits only for members busy
-// with earlier teams.
-void plan_teams(const std::vector<USig> &hs, const std::vector<int> &lpt, int grid, std::vector<UTask> &tasks,
-                std::vector<int> &task_start, std::vector<int> &small, int &nteams) {
-    double total = 0.0;
-    for (const USig &sg : hs) total += (double)sg.L * sg.L * sg.L;
-    const double share = grid > 0 ? total / grid : 1.0;
-    std::vector<std::vector<UTask>> per((size_t)std::max(grid, 1));
-    int cursor = 0;
-    nteams = 0;
-    for (int i : lpt) {
-        const double w = (double)hs[(size_t)i].L * hs[(size_t)i].L * hs[(size_t)i].L;
-        int T = hs[(size_t)i].L >= 64 ? (int)std::min<double>(kMaxTeam, std::floor(w / share)) : 1;
-        T = std::min(T, grid);
-        if (T < 2) { small.push_back(i); continue; }
-        if (cursor + T > grid) cursor = 0;
-        for (int r = 0; r < T; ++r) per[(size_t)(cursor + r)].push_back(UTask{i, r, T, nteams});
-        cursor += T;
-        ++nteams;
-    }
-    task_start.assign((size_t)grid + 1, 0);
-    for (int c = 0; c < grid; ++c) {
-        task_start[(size_t)c + 1] = task_start[(size_t)c] + (int)per[(size_t)c].size();
-        tasks.insert(tasks.end(), per[(size_t)c].begin(), per[(size_t)c].end());
-    }
-}
 
 template <typename K>
 cudaError_t coop_grid(K kernel, size_t smem, int *grid) {
@@ -700,7 +662,9 @@ sht_status sht_uneven_create(const sht_plan_t *plans, int nplans, int64_t nsig, 
     }
     std::vector<UTask> tasks;
     std::vector<int> task_start, small;
-    plan_teams(hs, lpt, u->grid_fwd, tasks, task_start, small, u->nteams);
+    std::vector<int> Ls((size_t)nsig);
+    for (int64_t i = 0; i < nsig; ++i) Ls[(size_t)i] = hs[(size_t)i].L;
+    plan_teams(Ls, lpt, u->grid_fwd, tasks, task_start, small, u->nteams);
     u->nsmall = (int)small.size();
     const size_t b_ws = sizeof(double) * (size_t)std::max<int64_t>(ws, 1);
     if ((e = cudaMalloc(&u->d_plans, sizeof(UPlan) * std::max<size_t>(hp.size(), 1))) != cudaSuccess ||
